@@ -1,0 +1,205 @@
+/*
+ * transec.h -- C ABI of the GB300 library for CAP-terminated Landauer transmission.
+ *
+ * The library computes, on one GPU, the k-resolved transmission of a real-space
+ * finite-difference Kohn-Sham Hamiltonian with lateral periodic boundaries and
+ * complex absorbing potentials (CAPs) at the two transport ends, following
+ * Zhu, Feldman & Dunham, arXiv 2208.02783 ("Highly parallelizable electronic
+ * transport calculations in periodic Rhodium and Copper nanostructures"):
+ *
+ *   G(E, k)  = [E - H_k + i(Gamma_L + Gamma_R)]^-1          (Sec. II.A)
+ *   T(E, k)  = 4 Tr[Gamma_L G^dagger Gamma_R G]             (Sec. II.A; the factor 4
+ *              goes with Gamma entering G as i*Gamma, so that T counts open channels)
+ *            = sum_{j : Gamma_L(j) > 0} t_j,
+ *   t_j      = 4 Gamma_L(j) sum_i Gamma_R(i) |x_j(i)|^2,    A(E, k) x_j = e_j
+ *   T(E)     = sum_k w_k T(E, k)                            (Sec. II.A, k-averaging)
+ *
+ * H_k (Sec. II.A, Eqs. Bloch and H_k) is -1/2 times the order-2N central
+ * finite-difference Laplacian plus the local potential V_KS, on a uniform grid with
+ * index n = i + nx*(j + ny*l); a lateral neighbour that leaves the cell re-enters on
+ * the other side with the Bloch factor exp(i k_a L_a w) (w = number of wraps), and
+ * z has zero Dirichlet ends.  The columns x_j are found with Krylov methods: COCG
+ * when H_k is real (kappa in {0, 1/2} on both axes, A complex symmetric), otherwise
+ * BiCG with the transposed shadow system -- the conjugate-orthogonal CG of the
+ * complex symmetric +-k operator of Sec. II.B (Eq. def-Gk) -- which also returns
+ * the columns of A(E, -k) = A(E, k)^T, hence T(E, -k), in the same run.
+ *
+ * Conventions for every entry point:
+ *   - Units are Hartree and bohr.  T is per spin (Sec. III).
+ *   - Host pointers unless stated; inputs are copied, never retained.
+ *   - The caller owns every output buffer.
+ *   - Each call returns a transec_status; on failure transec_last_error() describes
+ *     it.  No call traps or aborts: GPU-side failures come back as status codes.
+ *   - A context is not thread-safe; use one per host thread.  Work is queued on the
+ *     context's stream and every call below returns after its results are written.
+ */
+#ifndef TRANSEC_H
+#define TRANSEC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct transec_ctx transec_ctx;
+
+/* Status codes.  Per-result codes use the same values. */
+enum transec_status {
+  TRANSEC_OK = 0,
+  TRANSEC_EINVAL = -1,     /* bad argument (size, order, pointer, NaN input) */
+  TRANSEC_ENOMEM = -2,     /* device or host allocation failed */
+  TRANSEC_ECUDA = -3,      /* a CUDA call failed; see transec_last_error */
+  TRANSEC_ENOCONV = -4,    /* a column hit maxit before the tolerance; its t is NaN */
+  TRANSEC_EBREAKDOWN = -5, /* Krylov breakdown (zero or non-finite scalar); t is NaN */
+  TRANSEC_ETIMEOUT = -6,   /* a bounded device wait gave up */
+  TRANSEC_ESTATE = -7      /* call order violated (e.g. no potential set yet) */
+};
+
+/* Krylov method. */
+enum transec_method {
+  TRANSEC_METHOD_AUTO = 0, /* COCG where H_k is real, transpose BiCG elsewhere */
+  TRANSEC_METHOD_COCG = 1, /* only valid where H_k is real */
+  TRANSEC_METHOD_BICG = 2  /* transpose BiCG (+-k pair) everywhere */
+};
+
+/* Arithmetic of the iteration. */
+enum transec_precision {
+  TRANSEC_PREC_FP64 = 0,  /* complex128 vectors and stencil throughout */
+  TRANSEC_PREC_MIXED = 1  /* complex64 vectors and stencil with FP64 scalars, FP64
+                             solution accumulation and FP64 residual replacement */
+};
+
+typedef struct transec_solver_opts {
+  int method;         /* enum transec_method (default AUTO) */
+  int precision;      /* enum transec_precision (default FP64) */
+  double tol;         /* per column: ||A x - e_j||_2 <= tol (||e_j|| = 1); default 1e-10;
+                         BiCG requires the shadow residual to meet it too */
+  int maxit;          /* operator applications per half and column; default 100000 */
+  int slots;          /* columns in flight on the GPU; 0 = chosen by the autotuner */
+  int chunk;          /* iterations per graph launch between host polls; 0 = default */
+  double reliable;    /* mixed precision: replace the FP32 residual by the FP64 one
+                         when it has dropped by this factor; default 0.1 */
+  int tile_y;         /* stencil tile rows (0 = autotune); tiles span min(nx, 32) */
+  int slab;           /* z-planes per stencil block (0 = autotune) */
+  int profile;        /* != 0: time every stencil and update launch with CUDA events on
+                         the context's stream (read back with transec_stats) */
+} transec_solver_opts;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int transec_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* transec_status_string(int status);
+
+/*
+ * Create a context for an nx x ny x nz grid with spacings hx, hy, hz (bohr) and a
+ * finite-difference Laplacian of order fd_order in {2, 4, ..., 12} (Sec. I: the
+ * real-space grid Hamiltonian of PARSEC/TRANSEC).  device is a CUDA ordinal;
+ * cuda_stream is a cudaStream_t to order work after (NULL = the legacy default
+ * stream).  *out receives the context, or NULL on failure.
+ * Errors: EINVAL (sizes < 1, nz < 2, order not even in [2, 12], h <= 0),
+ *         ECUDA, ENOMEM.
+ */
+int transec_create(transec_ctx** out, int nx, int ny, int nz, double hx, double hy,
+                   double hz, int fd_order, int device, void* cuda_stream);
+
+/*
+ * Set the local Kohn-Sham potential V_KS (Sec. II.A, Eq. H_k), nx*ny*nz doubles in
+ * grid order (x fastest), Hartree.  on_device != 0 means v_ks is a device pointer
+ * on the context's device.  Errors: EINVAL (NULL, non-finite value), ECUDA.
+ */
+int transec_set_potential(transec_ctx* ctx, const double* v_ks, int on_device);
+
+/*
+ * Set the absorbing profiles Gamma_L(z), Gamma_R(z) (Sec. II.A, Eq. CAP-Gaussian:
+ * constant in the xy-plane, so one value per z-plane), nz doubles each, Hartree,
+ * host memory.  The left-CAP support {j : Gamma_L(plane(j)) > 0}, ordered by grid
+ * index, defines the right-hand sides e_j; its size is transec_n_rhs().
+ * Errors: EINVAL (NULL, negative or non-finite value, empty left support).
+ */
+int transec_set_abc(transec_ctx* ctx, const double* gamma_l, const double* gamma_r);
+
+/*
+ * Set the lateral k-mesh (Sec. II.A: T(E) is the average of T_k(E) over sampled k).
+ * kfrac holds nk pairs (k_a L_a / 2pi, k_b L_b / 2pi); weights holds nk values
+ * (NULL = uniform 1/nk).  Host memory.  Errors: EINVAL (nk < 1, non-finite).
+ */
+int transec_set_kmesh(transec_ctx* ctx, int nk, const double* kfrac, const double* weights);
+
+/* Replace / read the solver options (fields left 0 take their defaults). */
+int transec_set_solver(transec_ctx* ctx, const transec_solver_opts* opts);
+int transec_get_solver(const transec_ctx* ctx, transec_solver_opts* opts);
+
+/* Number of left-CAP columns (right-hand sides per (E, k)). */
+int transec_n_rhs(const transec_ctx* ctx, int64_t* n_rhs);
+
+/*
+ * Full transmission: for every energy energies[e] (Hartree) and every k of the mesh,
+ * solve all left-CAP columns and write T_out[e*nk + k] = T(E_e, k).  If T_avg_out is
+ * not NULL it receives T(E_e) = sum_k w_k T(E_e, k).  status_out (ne*nk ints, may be
+ * NULL) receives the worst status over that (E, k)'s columns; iters_out (ne*nk ints,
+ * may be NULL) the largest iteration count.  With BiCG, a k whose mirror -k is also
+ * in the mesh is not solved again: T(E, -k) comes from the shadow columns of k.
+ * An (E, k) with a failed column gets T = NaN; the call then returns the most
+ * severe status and every other result stays valid.  Host memory.
+ */
+int transec_transmission(transec_ctx* ctx, int ne, const double* energies, double* T_out,
+                         double* T_avg_out, int* status_out, int* iters_out);
+
+/*
+ * Sampled columns: for item i, solve A(energies[i], k_{ik[i]}) x = e_j with j the
+ * cols[i]-th left-CAP column (0 <= cols[i] < n_rhs) and write t_out[i] = t_j.  If
+ * t_minus_out is not NULL it receives t_j at (E, -k) (from the BiCG shadow column;
+ * equal to t_out where H_k is real).  iters_out / status_out (may be NULL) receive
+ * per-item iteration counts and statuses.  With on_device != 0 every array argument
+ * is a device pointer on the context's device (energies double, ik int32, cols int64,
+ * outputs double / int32); otherwise host memory.  Returns the most severe status.
+ */
+int transec_column_contributions(transec_ctx* ctx, int nitems, const double* energies,
+                                 const int* ik, const int64_t* cols, double* t_out,
+                                 double* t_minus_out, int* iters_out, int* status_out,
+                                 int on_device);
+
+/*
+ * Operator apply (the hot-path stencil on its own): y_v = A(E, k_ik) x_v for nvec
+ * vectors of nx*ny*nz complex128 values (interleaved re, im; grid order), stored
+ * one after another.  conj_k != 0 applies A(E, -k) = A(E, k)^T instead.  Device
+ * pointers (on_device != 0) or host memory.  Used to check the stencil on its own.
+ */
+int transec_apply(transec_ctx* ctx, double energy, int ik, int conj_k, int nvec,
+                  const double* x, double* y, int on_device);
+
+/*
+ * Column trace (the reduction on its own): for nvec solution vectors x_v (complex128,
+ * grid order, one after another) and left-CAP column positions cols[v], write
+ * t_out[v] = 4 Gamma_L(j_v) sum_i Gamma_R(i) |x_v(i)|^2.  Device or host memory.
+ */
+int transec_trace(transec_ctx* ctx, int nvec, const double* x, const int64_t* cols,
+                  double* t_out, int on_device);
+
+/*
+ * Counters of the solves since the last transec_stats_reset (or creation):
+ * launches = library kernels launched; point_applies = operator applications summed
+ * over columns and halves, times grid points (the work the stencil did); with
+ * opts.profile set, stencil_ms / update_ms = summed device time of the stencil and
+ * vector-update launches and stencil_launches / update_launches their counts.  Any
+ * output pointer may be NULL.
+ */
+int transec_stats(const transec_ctx* ctx, long long* launches, long long* point_applies,
+                  double* stencil_ms, long long* stencil_launches, double* update_ms,
+                  long long* update_launches);
+int transec_stats_reset(transec_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  Valid until the next
+ * call on the same context. */
+const char* transec_last_error(const transec_ctx* ctx);
+
+/* Release the context and everything it allocated.  NULL is ignored. */
+void transec_destroy(transec_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRANSEC_H */

@@ -118,7 +118,7 @@ def cocg(a, b, tol, maxit):
     return x, its
 
 
-def bicg_transpose(a, b, tol, maxit):
+def bicg_transpose(a, b, tol, maxit, mark_tol=None):
     """BiCG whose shadow system is the transpose: A x = b and A^T y = b together.
 
     Since A(E, k)^T = A(E, -k) (H_{-k} = H_k^*, Sec. II.B), the shadow solution is
@@ -127,6 +127,8 @@ def bicg_transpose(a, b, tol, maxit):
     +-k pair), with the bilinear forms y^T x.  Textbook BiCG (Fletcher 1976) with
     r_hat_0 = r_0 = b, per column; a column stops once both residual norms are at
     most tol ||b||_2.  Returns (x, y, iterations; negative where maxit was reached).
+    With ``mark_tol`` set, also returns the first iteration at which both residuals
+    were at most mark_tol ||b||_2 (a looser tolerance reached on the way).
     """
     at = a.T.tocsr()
     x = np.zeros_like(b)
@@ -138,6 +140,7 @@ def bicg_transpose(a, b, tol, maxit):
     rho = np.einsum("ij,ij->j", rs, r)
     nb = np.linalg.norm(b, axis=0)
     its = np.full(b.shape[1], -maxit)
+    marks = np.full(b.shape[1], -maxit)
     live = np.ones(b.shape[1], bool)
     for it in range(1, maxit + 1):
         L = live
@@ -151,6 +154,9 @@ def bicg_transpose(a, b, tol, maxit):
         rn = np.maximum(np.linalg.norm(r[:, L], axis=0), np.linalg.norm(rs[:, L], axis=0))
         done = rn <= tol * nb[L]
         idx = np.nonzero(L)[0]
+        if mark_tol is not None:
+            hit = (rn <= mark_tol * nb[L]) & (marks[idx] < 0)
+            marks[idx[hit]] = it
         its[idx[done]] = it
         live = L.copy()
         live[idx[done]] = False
@@ -161,6 +167,8 @@ def bicg_transpose(a, b, tol, maxit):
         p[:, live] = r[:, live] + beta * p[:, live]
         ps[:, live] = rs[:, live] + beta * ps[:, live]
         rho[live] = rho_new
+    if mark_tol is not None:
+        return x, y, its, marks
     return x, y, its
 
 

@@ -1,0 +1,307 @@
+"""ctypes binding of the C ABI in include/transec.h.
+
+Argument marshalling only: every function here converts its arguments to plain
+pointers and sizes and calls the entry point of the same name in libtransec.so.
+All arithmetic happens in the library's CUDA kernels; there is no fallback, and
+loading fails loudly when the library has not been built.
+
+Arrays may be NumPy arrays (host memory) or torch tensors (host or CUDA memory).
+A call takes all of its array arguments from one side: either every array is a
+CUDA tensor (``on_device`` = 1) or none is.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_native", "libtransec.so")
+
+# status codes (enum transec_status)
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+METHOD_AUTO, METHOD_COCG, METHOD_BICG = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class TransecError(RuntimeError):
+    """A library call returned a non-zero status."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [
+        ("method", C.c_int),
+        ("precision", C.c_int),
+        ("tol", C.c_double),
+        ("maxit", C.c_int),
+        ("slots", C.c_int),
+        ("chunk", C.c_int),
+        ("reliable", C.c_double),
+        ("tile_y", C.c_int),
+        ("slab", C.c_int),
+        ("profile", C.c_int),
+    ]
+
+
+_lib = None
+
+_P = C.c_void_p
+_SIGS = {
+    "transec_version": (C.c_int, []),
+    "transec_status_string": (C.c_char_p, [C.c_int]),
+    "transec_create": (
+        C.c_int,
+        [C.POINTER(_P), C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int, _P],
+    ),
+    "transec_set_potential": (C.c_int, [_P, _P, C.c_int]),
+    "transec_set_abc": (C.c_int, [_P, _P, _P]),
+    "transec_set_kmesh": (C.c_int, [_P, C.c_int, _P, _P]),
+    "transec_set_solver": (C.c_int, [_P, C.POINTER(SolverOpts)]),
+    "transec_get_solver": (C.c_int, [_P, C.POINTER(SolverOpts)]),
+    "transec_n_rhs": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "transec_transmission": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
+    "transec_column_contributions": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int]),
+    "transec_apply": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "transec_trace": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
+    "transec_stats": (C.c_int, [_P] + [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "transec_stats_reset": (C.c_int, [_P]),
+    "transec_last_error": (C.c_char_p, [_P]),
+    "transec_destroy": (None, [_P]),
+}
+
+EXPORTED = tuple(_SIGS)
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libtransec.so (built by paper_2208_02783_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build it with `python -m paper_2208_02783_gb300.build` "
+            "(the library has no CPU fallback)"
+        )
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, status: int, what: str, allow=()):
+    if status == OK or status in allow:
+        return status
+    lib = load()
+    msg = lib.transec_last_error(ctx).decode() if ctx else ""
+    if allow and msg.startswith("some "):
+        # per-result failures: the status arrays say which results failed
+        return status
+    raise TransecError(status, f"{what}: {lib.transec_status_string(status).decode()}: {msg}")
+
+
+class _Arr:
+    """Pointer view of a NumPy array or torch tensor with a required dtype."""
+
+    def __init__(self, a, dtype, writable=False):
+        self.device = False
+        self.keep = None
+        try:
+            import torch  # noqa: F401
+
+            is_torch = hasattr(a, "data_ptr") and hasattr(a, "is_cuda")
+        except ImportError:  # pragma: no cover
+            is_torch = False
+        if is_torch:
+            tdt = {np.float64: "torch.float64", np.int32: "torch.int32", np.int64: "torch.int64"}[dtype]
+            if str(a.dtype) != tdt:
+                raise TypeError(f"expected {tdt}, got {a.dtype}")
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            self.device = bool(a.is_cuda)
+            self.keep = a
+            self.ptr = C.c_void_p(a.data_ptr())
+        else:
+            arr = np.asarray(a)
+            if writable:
+                if arr.dtype != dtype or not arr.flags.c_contiguous:
+                    raise TypeError(f"output must be a C-contiguous {np.dtype(dtype)} array")
+            else:
+                arr = np.ascontiguousarray(arr, dtype=dtype)
+            self.keep = arr
+            self.ptr = arr.ctypes.data_as(C.c_void_p)
+
+
+def _side(arrs):
+    dev = {x.device for x in arrs if x is not None}
+    if len(dev) > 1:
+        raise ValueError("mixing host and device arrays in one call")
+    return 1 if dev == {True} else 0
+
+
+def _complex_view(x):
+    """complex128 NumPy array -> float64 view; torch complex128 -> view_as_real."""
+    if hasattr(x, "is_cuda"):
+        import torch
+
+        if x.dtype == torch.complex128:
+            return torch.view_as_real(x)
+        return x
+    x = np.ascontiguousarray(x)
+    if x.dtype == np.complex128:
+        return x.view(np.float64)
+    return x
+
+
+# ----------------------------------------------------------------------------------
+# the entry points, one per C function
+# ----------------------------------------------------------------------------------
+
+
+def transec_version() -> int:
+    return load().transec_version()
+
+
+def transec_status_string(status: int) -> str:
+    return load().transec_status_string(status).decode()
+
+
+def transec_create(nx, ny, nz, hx, hy, hz, fd_order, device=0, stream=None):
+    lib = load()
+    out = C.c_void_p()
+    st = lib.transec_create(C.byref(out), nx, ny, nz, hx, hy, hz, fd_order, device,
+                            C.c_void_p(stream) if stream else None)
+    if st != OK:
+        raise TransecError(st, f"transec_create: {lib.transec_status_string(st).decode()}")
+    _NPOINTS[out.value] = int(nx) * int(ny) * int(nz)
+    return out
+
+
+def transec_set_potential(ctx, v_ks):
+    a = _Arr(v_ks, np.float64)
+    return _check(ctx, load().transec_set_potential(ctx, a.ptr, _side([a])), "transec_set_potential")
+
+
+def transec_set_abc(ctx, gamma_l, gamma_r):
+    a = _Arr(np.asarray(gamma_l, np.float64), np.float64)
+    b = _Arr(np.asarray(gamma_r, np.float64), np.float64)
+    return _check(ctx, load().transec_set_abc(ctx, a.ptr, b.ptr), "transec_set_abc")
+
+
+def transec_set_kmesh(ctx, kfrac, weights=None):
+    k = _Arr(np.asarray(kfrac, np.float64).reshape(-1, 2), np.float64)
+    nk = k.keep.shape[0]
+    w = _Arr(np.asarray(weights, np.float64), np.float64) if weights is not None else None
+    return _check(ctx, load().transec_set_kmesh(ctx, nk, k.ptr, w.ptr if w else None), "transec_set_kmesh")
+
+
+def transec_set_solver(ctx, opts: SolverOpts):
+    return _check(ctx, load().transec_set_solver(ctx, C.byref(opts)), "transec_set_solver")
+
+
+def transec_get_solver(ctx) -> SolverOpts:
+    o = SolverOpts()
+    _check(ctx, load().transec_get_solver(ctx, C.byref(o)), "transec_get_solver")
+    return o
+
+
+def transec_n_rhs(ctx) -> int:
+    n = C.c_int64()
+    _check(ctx, load().transec_n_rhs(ctx, C.byref(n)), "transec_n_rhs")
+    return int(n.value)
+
+
+def transec_transmission(ctx, energies, T_out, T_avg_out=None, status_out=None, iters_out=None):
+    e = _Arr(energies, np.float64)
+    t = _Arr(T_out, np.float64, writable=True)
+    ta = _Arr(T_avg_out, np.float64, writable=True) if T_avg_out is not None else None
+    so = _Arr(status_out, np.int32, writable=True) if status_out is not None else None
+    io = _Arr(iters_out, np.int32, writable=True) if iters_out is not None else None
+    if _side([e, t, ta, so, io]):
+        raise ValueError("transec_transmission takes host arrays")
+    ne = int(np.asarray(e.keep).size)
+    st = load().transec_transmission(
+        ctx, ne, e.ptr, t.ptr, ta.ptr if ta else None, so.ptr if so else None, io.ptr if io else None
+    )
+    return _check(ctx, st, "transec_transmission", allow=(ENOCONV, EBREAKDOWN))
+
+
+def transec_column_contributions(ctx, energies, ik, cols, t_out, t_minus_out=None, iters_out=None,
+                                 status_out=None):
+    e = _Arr(energies, np.float64)
+    k = _Arr(ik, np.int32)
+    c = _Arr(cols, np.int64)
+    t = _Arr(t_out, np.float64, writable=True)
+    tm = _Arr(t_minus_out, np.float64, writable=True) if t_minus_out is not None else None
+    io = _Arr(iters_out, np.int32, writable=True) if iters_out is not None else None
+    so = _Arr(status_out, np.int32, writable=True) if status_out is not None else None
+    side = _side([e, k, c, t, tm, io, so])
+    n = int(e.keep.numel() if hasattr(e.keep, "numel") else np.asarray(e.keep).size)
+    st = load().transec_column_contributions(
+        ctx, n, e.ptr, k.ptr, c.ptr, t.ptr, tm.ptr if tm else None, io.ptr if io else None,
+        so.ptr if so else None, side,
+    )
+    return _check(ctx, st, "transec_column_contributions", allow=(ENOCONV, EBREAKDOWN))
+
+
+def transec_apply(ctx, energy, ik, x, y, conj_k=False):
+    xv = _complex_view(x)
+    yv = _complex_view(y)
+    a = _Arr(xv, np.float64)
+    b = _Arr(yv, np.float64, writable=True)
+    side = _side([a, b])
+    n_el = int(a.keep.numel() if hasattr(a.keep, "numel") else a.keep.size)
+    g = transec_n_points(ctx)
+    nvec = n_el // (2 * g)
+    st = load().transec_apply(ctx, float(energy), int(ik), 1 if conj_k else 0, nvec, a.ptr, b.ptr, side)
+    return _check(ctx, st, "transec_apply")
+
+
+def transec_trace(ctx, x, cols, t_out):
+    xv = _complex_view(x)
+    a = _Arr(xv, np.float64)
+    c = _Arr(cols, np.int64)
+    t = _Arr(t_out, np.float64, writable=True)
+    side = _side([a, c, t])
+    nvec = int(c.keep.numel() if hasattr(c.keep, "numel") else np.asarray(c.keep).size)
+    st = load().transec_trace(ctx, nvec, a.ptr, c.ptr, t.ptr, side)
+    return _check(ctx, st, "transec_trace")
+
+
+def transec_stats(ctx) -> dict:
+    v = [C.c_longlong(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong()]
+    _check(ctx, load().transec_stats(ctx, *[C.byref(x) for x in v]), "transec_stats")
+    keys = ("launches", "point_applies", "stencil_ms", "stencil_launches", "update_ms", "update_launches")
+    return {k: x.value for k, x in zip(keys, v)}
+
+
+def transec_stats_reset(ctx):
+    return _check(ctx, load().transec_stats_reset(ctx), "transec_stats_reset")
+
+
+def transec_last_error(ctx) -> str:
+    return load().transec_last_error(ctx).decode()
+
+
+def transec_destroy(ctx):
+    if ctx:
+        _NPOINTS.pop(ctx.value, None)
+        load().transec_destroy(ctx)
+
+
+# grid size bookkeeping for transec_apply (kept on the Python side of the handle)
+_NPOINTS: dict[int, int] = {}
+
+
+def transec_n_points(ctx) -> int:
+    return _NPOINTS[ctx.value]

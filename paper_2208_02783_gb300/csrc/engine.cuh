@@ -1,0 +1,98 @@
+// Host-side declarations shared by the C ABI and the solver engines.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/transec.h"
+#include "kernels.cuh"
+
+struct transec_ctx;
+
+namespace transec {
+
+// Device buffers and launch shape of one slot engine (one arithmetic type T, one
+// number of halves H).  Buffers are kept between calls and grown on demand.
+template <typename T>
+struct Engine {
+  using CT = typename Cx<T>::type;
+  int S = 0, H = 0;
+  long long n = 0;
+  CT* X = nullptr;
+  CT* R = nullptr;
+  CT* P0 = nullptr;
+  CT* P1 = nullptr;
+  CT* Q = nullptr;
+  double* sig_part = nullptr;
+  double* rho_part = nullptr;
+  Slot* slots = nullptr;
+  Queue* queue = nullptr;
+  // stencil launch shape
+  int TX = 0, TY = 0, D = 0, ntx = 0, nty = 0, nslab = 0, threads = 0;
+  size_t smem = 0;
+  int nblk2 = 0, nblk3 = 0;
+  void release();
+};
+
+// Launch shape of the stencil for a geometry.
+struct TileShape {
+  int TX, TY, D, ntx, nty, nslab, threads;
+  size_t smem;
+};
+
+TileShape choose_tiles(const Geometry& g, int H, int elem_bytes, int max_threads, int tile_y,
+                       int slab);
+
+template <typename T>
+void launch_stencil(int R, dim3 grid, int threads, size_t smem, cudaStream_t s,
+                    const StencilArgs<T>& a);
+
+}  // namespace transec
+
+// The context behind the opaque C handle.
+struct transec_ctx {
+  int device = 0;
+  cudaStream_t user = nullptr;  // caller's stream (may be the legacy default stream)
+  cudaStream_t s = nullptr;     // the context's own stream (graph capture happens here)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  transec::Geometry g{};
+  int order = 0;
+  double hx = 0, hy = 0, hz = 0;
+  // operator data
+  double* d_v = nullptr;
+  float* d_v32 = nullptr;
+  bool have_v = false;
+  std::vector<double> gl, gr;
+  double* d_gl = nullptr;
+  double* d_gr = nullptr;
+  double* d_gam = nullptr;
+  int* d_lplanes = nullptr;
+  int* d_rplanes = nullptr;
+  std::vector<int> lplanes, rplanes;
+  bool have_abc = false;
+  int nk = 0;
+  std::vector<double> kfrac, kw;
+  double2* d_phase = nullptr;
+  bool have_k = false;
+  transec_solver_opts opts{};
+  std::string err;
+  // solver engines
+  transec::Engine<double> e64;
+  transec::Engine<float> e32;
+  // mixed precision extra FP64 state: solution and residual per slot/half
+  double2* mx_x = nullptr;
+  double2* mx_r = nullptr;
+  long long mx_elems = 0;
+  double* mx_part = nullptr;
+  long long mx_part_elems = 0;
+  // pinned host word for the harvested counter
+  int* h_harvest = nullptr;
+  // counters since the last transec_stats_reset
+  long long launches = 0;
+  long long point_applies = 0;
+  double stencil_ms = 0, update_ms = 0;
+  long long stencil_launches = 0, update_launches = 0;
+  std::vector<cudaEvent_t> prof_ev;  // 4 per iteration of a chunk when profiling
+};

@@ -1,0 +1,573 @@
+// CUDA kernels of the transmission hot path (sm_103a).
+//
+//   k_stencil   Bloch-phased stencil apply fused with the Krylov pre-update:
+//               p <- r + beta p, q <- A(E, +-k) p, sigma += <p, q> (pairing form)
+//   k_update    x += alpha p, r -= alpha q, rho' = <r, r>, ||r_h||^2 per half
+//   k_scalars   per slot: reduce the partial sums, convergence, beta = rho'/rho
+//   k_trace     t_j = 4 Gamma_L(j) sum_i Gamma_R(i) |x_j(i)|^2 for finished slots
+//   k_assign    hand queued (E, k, column) items to idle slots
+//   k_init      x = 0, r = e_j, p = 0 for newly assigned slots
+//
+// The operator (paper Sec. II.A, Eqs. Bloch and H_k) is
+//   A(E, k) p = (E - V + c_0/2 sum_a h_a^-2 + i Gamma) p
+//             + sum_a sum_{m=1..R} c_m/(2 h_a^2) (p(n + m e_a) + p(n - m e_a)),
+// a lateral neighbour that leaves the cell re-entering on the other side with the
+// Bloch factor exp(2 pi i kappa_a w) (w = wrap count), z-neighbours outside the grid
+// being zero.  half 1 of a transpose-BiCG slot applies A(E, -k) = A(E, k)^T, i.e.
+// the conjugate phases (Sec. II.B, H_{-k} = H_k^*).
+//
+// Reductions are deterministic: every block writes one partial per quantity and
+// the consumer sums the partials in a fixed order.
+#pragma once
+
+#include "common.cuh"
+
+namespace transec {
+
+// ---------------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------------
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of NV doubles per thread; the result is valid in thread 0.
+template <int NV>
+__device__ inline void block_sum(double (&v)[NV], double (*red)[32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[k][wid] = v[k];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = lane < nw ? red[k][lane] : 0.0;
+      v[k] = warp_sum(s);
+    }
+  }
+}
+
+__device__ inline int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------------
+// stencil apply fused with p <- r + beta p
+// ---------------------------------------------------------------------------------
+
+template <typename T>
+struct StencilArgs {
+  using CT = typename Cx<T>::type;
+  const CT* r;          // [slot][half][n]
+  const CT* p_in;       // previous search direction
+  CT* p_out;            // p_in + beta... written as r + beta p_in
+  CT* q;                // A p_out
+  double* part;         // [slot][nblk][2] partial sums of <p, A p>
+  const Slot* slots;
+  const double2* phase; // [nk][2 (sign of k)][2 (axis)][kPhaseN]
+  const T* v;           // potential in the arithmetic type
+  const double* gam;    // Gamma_L + Gamma_R per plane
+  Geometry g;
+  int H, TX, TY, D, ntx;
+  int conj;             // 1: swap the phase tables (apply A^T to half 0)
+  long long slot_stride;  // H * n
+};
+
+// Block = TX*TY*H threads (rounded up to whole warps), one grid point (x, y) per thread and half, marching over
+// the z-slab [z0, z0 + D) with a register queue of the 2R+1 planes around the
+// centre plane; the centre plane (plus lateral halos, Bloch-phased when wrapped)
+// sits in shared memory for the x/y neighbours.  Grid = (tiles, slabs, slots).
+// Threads per stencil block: FP64 keeps the 13-plane queue in 128 registers.
+template <typename T> struct StencilMax { static constexpr int threads = 768; };
+template <> struct StencilMax<double> { static constexpr int threads = 512; };
+
+template <typename T, int R>
+__global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const StencilArgs<T> a) {
+  using CT = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[2][32];
+  CT* sm = reinterpret_cast<CT*>(smem_raw);
+
+  const int slot = blockIdx.z;
+  const Slot* stp = a.slots + slot;
+  if (stp->status != SLOT_ACTIVE) return;  // uniform over the block
+  const double2 beta_d = stp->beta;
+  const double e = stp->e;
+  const int ik = stp->ik;
+
+  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
+  const long long nxy = a.g.nxy;
+  const int npt = a.TX * a.TY;
+  const int t = threadIdx.x;
+  // the block is rounded up to whole warps; threads past TX*TY*H only join the
+  // barriers and the reductions
+  const bool worker = t < npt * a.H;
+  const int half = worker ? t / npt : 0;
+  const int lt = worker ? t - half * npt : 0;
+  const int tx = lt % a.TX, ty = lt / a.TX;
+  const int x0 = (blockIdx.x % a.ntx) * a.TX, y0 = (blockIdx.x / a.ntx) * a.TY;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool inside = worker && (gx < nx) && (gy < ny);
+  const int z0 = blockIdx.y * a.D;
+  const int z1 = min(z0 + a.D, nz);
+  const int SW = a.TX + 2 * R;
+  const int SHt = a.TY + 2 * R;
+  CT* my = sm + half * SW * SHt;
+  const long long base = (long long)slot * a.slot_stride + (long long)half * a.g.n;
+  const CT* __restrict__ r = a.r + base;
+  const CT* __restrict__ pin = a.p_in + base;
+  CT* __restrict__ pout = a.p_out + base;
+  CT* __restrict__ q = a.q + base;
+  const CT beta = cfrom<CT>(beta_d);
+  const double2* ph = a.phase + (size_t)(ik * 2 + (half ^ a.conj)) * 2 * kPhaseN;
+  const long long pidx = (long long)gx + (long long)nx * gy;
+
+  T kx[R + 1], ky[R + 1], kz[R + 1];
+#pragma unroll
+  for (int m = 1; m <= R; ++m) {
+    kx[m] = (T)a.g.kx[m];
+    ky[m] = (T)a.g.ky[m];
+    kz[m] = (T)a.g.kz[m];
+  }
+  const T ediag = (T)(e + a.g.diag_c);
+
+  auto pnew = [&](long long off) -> CT {
+    const CT rr = r[off], pp = pin[off];
+    CT o;
+    o.x = rr.x + beta.x * pp.x - beta.y * pp.y;
+    o.y = rr.y + beta.x * pp.y + beta.y * pp.x;
+    return o;
+  };
+  // p_new at an arbitrary lateral position of plane zc, wrapped into the cell with
+  // its Bloch factor (Eq. Bloch: phi(x + L) = exp(i k L) phi(x)).
+  auto wrapped = [&](int xx, int yy, int zc) -> CT {
+    int wx = 0, wy = 0;
+    if (xx < 0 || xx >= nx) { wx = floordiv(xx, nx); xx -= wx * nx; }
+    if (yy < 0 || yy >= ny) { wy = floordiv(yy, ny); yy -= wy * ny; }
+    CT v = pnew((long long)zc * nxy + xx + (long long)nx * yy);
+    if (wx) v = cmul(v, cfrom<CT>(ph[kPhaseW + wx]));
+    if (wy) v = cmul(v, cfrom<CT>(ph[kPhaseN + kPhaseW + wy]));
+    return v;
+  };
+
+  CT qv[2 * R + 1];
+  qv[0] = czero<CT>();
+#pragma unroll
+  for (int m = 1; m <= 2 * R; ++m) {
+    const int z = z0 - R + m - 1;
+    qv[m] = (inside && z >= 0 && z < nz) ? pnew((long long)z * nxy + pidx) : czero<CT>();
+  }
+
+  T sgx = 0, sgy = 0;
+  const int nh = 2 * R * (a.TX + a.TY);
+  for (int zc = z0; zc < z1; ++zc) {
+#pragma unroll
+    for (int m = 0; m < 2 * R; ++m) qv[m] = qv[m + 1];
+    {
+      const int z = zc + R;
+      qv[2 * R] = (inside && z < nz) ? pnew((long long)z * nxy + pidx) : czero<CT>();
+    }
+    const CT c = qv[R];
+    if (worker) my[(ty + R) * SW + tx + R] = inside ? c : wrapped(gx, gy, zc);
+    for (int h = worker ? lt : nh; h < nh; h += npt) {
+      int hx, hy;
+      if (h < 2 * R * a.TY) {
+        const int row = h / (2 * R), k = h - row * 2 * R;
+        hy = row + R;
+        hx = (k < R) ? k : a.TX + k;
+      } else {
+        const int h2 = h - 2 * R * a.TY;
+        const int col = h2 / (2 * R), k = h2 - col * 2 * R;
+        hx = col + R;
+        hy = (k < R) ? k : a.TY + k;
+      }
+      my[hy * SW + hx] = wrapped(x0 + hx - R, y0 + hy - R, zc);
+    }
+    __syncthreads();
+    if (inside) {
+      const long long off = (long long)zc * nxy + pidx;
+      const T dr = ediag - a.v[off];
+      const T di = (T)a.gam[zc];
+      CT acc;
+      acc.x = dr * c.x - di * c.y;
+      acc.y = dr * c.y + di * c.x;
+      const CT* ctr = my + (ty + R) * SW + (tx + R);
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const CT xa = ctr[m], xb = ctr[-m], ya = ctr[m * SW], yb = ctr[-m * SW];
+        const CT za = qv[R + m], zb = qv[R - m];
+        acc.x += kx[m] * (xa.x + xb.x) + ky[m] * (ya.x + yb.x) + kz[m] * (za.x + zb.x);
+        acc.y += kx[m] * (xa.y + xb.y) + ky[m] * (ya.y + yb.y) + kz[m] * (za.y + zb.y);
+      }
+      q[off] = acc;
+      pout[off] = c;
+      // pairing form: half h pairs with half 1-h at the same point (or itself)
+      const CT o = (a.H == 2) ? sm[(1 - half) * SW * SHt + (ty + R) * SW + tx + R] : c;
+      sgx += o.x * acc.x - o.y * acc.y;
+      sgy += o.x * acc.y + o.y * acc.x;
+    }
+    __syncthreads();
+  }
+  double v2[2] = {(double)sgx, (double)sgy};
+  block_sum<2>(v2, red);
+  if (threadIdx.x == 0) {
+    const int nblk = gridDim.x * gridDim.y;
+    const int b = blockIdx.x + gridDim.x * blockIdx.y;
+    double* o = a.part + ((size_t)slot * nblk + b) * 2;
+    o[0] = v2[0];
+    o[1] = v2[1];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// vector update: x += alpha p, r -= alpha q, partial <r, r> and ||r_h||^2
+// ---------------------------------------------------------------------------------
+
+template <typename T>
+struct UpdateArgs {
+  using CT = typename Cx<T>::type;
+  CT* x;
+  CT* r;
+  const CT* p;
+  const CT* q;
+  const double* sig_part;  // [slot][sig_nblk][2]
+  int sig_nblk;
+  double* rho_part;        // [slot][gridDim.x][4]: rho re, rho im, |r_0|^2, |r_1|^2
+  const Slot* slots;
+  long long n, slot_stride;
+  int H;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(const UpdateArgs<T> a) {
+  using CT = typename Cx<T>::type;
+  __shared__ double red[4][32];
+  __shared__ double2 s_alpha;
+  const int slot = blockIdx.y;
+  const Slot* stp = a.slots + slot;
+  if (stp->status != SLOT_ACTIVE) return;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    double sx = 0.0, sy = 0.0;
+    const double* sp = a.sig_part + (size_t)slot * a.sig_nblk * 2;
+    for (int b = lane; b < a.sig_nblk; b += 32) {
+      sx += sp[2 * b];
+      sy += sp[2 * b + 1];
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (lane == 0) s_alpha = cdiv(stp->rho, make_double2(sx, sy));
+  }
+  __syncthreads();
+  const CT al = cfrom<CT>(s_alpha);
+  const long long base = (long long)slot * a.slot_stride;
+  T rrx = 0, rry = 0, n0 = 0, n1 = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    CT rv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h >= a.H) break;
+      const long long off = base + (long long)h * a.n + i;
+      const CT pp = a.p[off], qq = a.q[off];
+      CT xx = a.x[off], rr = a.r[off];
+      xx.x += al.x * pp.x - al.y * pp.y;
+      xx.y += al.x * pp.y + al.y * pp.x;
+      rr.x -= al.x * qq.x - al.y * qq.y;
+      rr.y -= al.x * qq.y + al.y * qq.x;
+      a.x[off] = xx;
+      a.r[off] = rr;
+      rv[h] = rr;
+    }
+    n0 += rv[0].x * rv[0].x + rv[0].y * rv[0].y;
+    if (a.H == 2) {
+      n1 += rv[1].x * rv[1].x + rv[1].y * rv[1].y;
+      // <r, r> = r_+ . r_- + r_- . r_+ = 2 r_+ . r_-
+      rrx += 2 * (rv[0].x * rv[1].x - rv[0].y * rv[1].y);
+      rry += 2 * (rv[0].x * rv[1].y + rv[0].y * rv[1].x);
+    } else {
+      rrx += rv[0].x * rv[0].x - rv[0].y * rv[0].y;
+      rry += 2 * rv[0].x * rv[0].y;
+    }
+  }
+  double v4[4] = {(double)rrx, (double)rry, (double)n0, (double)n1};
+  block_sum<4>(v4, red);
+  if (threadIdx.x == 0) {
+    double* o = a.rho_part + ((size_t)slot * gridDim.x + blockIdx.x) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[k] = v4[k];
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// per-slot scalars: one warp per slot
+// ---------------------------------------------------------------------------------
+
+struct ScalarArgs {
+  const double* rho_part;  // [slot][nblk][4]
+  int nblk;
+  Slot* slots;
+  int S, H, maxit;
+  double tol;
+};
+
+// Status codes written to Slot::result (same values as the C ABI).
+constexpr int kOK = 0, kEINVAL = -1, kENOCONV = -4, kEBREAKDOWN = -5;
+
+static __global__ void __launch_bounds__(256) k_scalars(const ScalarArgs a) {
+  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (slot >= a.S) return;
+  Slot* st = a.slots + slot;
+  if (st->status != SLOT_ACTIVE) return;
+  double s[4] = {0, 0, 0, 0};
+  const double* rp = a.rho_part + (size_t)slot * a.nblk * 4;
+  for (int b = lane; b < a.nblk; b += 32)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s[k] += rp[4 * b + k];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s[k] = warp_sum(s[k]);
+  if (lane != 0) return;
+  const double2 rho_new = make_double2(s[0], s[1]);
+  const int it = st->it + 1;
+  const double res = sqrt(a.H == 2 ? fmax(s[2], s[3]) : s[2]);
+  int code = 1;  // still running
+  if (!isfinite(rho_new.x) || !isfinite(rho_new.y) || !isfinite(res)) code = kEBREAKDOWN;
+  else if (res <= a.tol) code = kOK;
+  else if (rho_new.x == 0.0 && rho_new.y == 0.0) code = kEBREAKDOWN;
+  else if (it >= a.maxit) code = kENOCONV;
+  st->it = it;
+  st->res = res;
+  if (code != 1) {
+    st->result = code;
+    st->status = SLOT_DONE;
+  } else {
+    st->beta = cdiv(rho_new, st->rho);
+    st->rho = rho_new;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// trace of finished slots, results, slot release
+// ---------------------------------------------------------------------------------
+
+template <typename TX>
+struct TraceArgs {
+  using CT = typename Cx<TX>::type;
+  const CT* x;             // [slot][half][n]
+  Slot* slots;
+  Queue* queue;
+  const int* rplanes;      // planes with Gamma_R > 0
+  int nrp;
+  const double* gl;        // Gamma_L per plane
+  const double* gr;        // Gamma_R per plane
+  double* res_t;
+  double* res_tm;
+  int* res_it;
+  int* res_status;
+  long long nxy, n, slot_stride;
+  int H;
+};
+
+template <typename TX>
+__global__ void __launch_bounds__(256) k_trace(const TraceArgs<TX> a) {
+  using CT = typename Cx<TX>::type;
+  __shared__ double red[2][32];
+  const int slot = blockIdx.x;
+  Slot* st = a.slots + slot;
+  if (st->status != SLOT_DONE) return;
+  double acc[2] = {0.0, 0.0};
+  const long long tot = (long long)a.nrp * a.nxy;
+  for (int h = 0; h < a.H; ++h) {
+    const CT* x = a.x + (long long)slot * a.slot_stride + (long long)h * a.n;
+    double s = 0.0;
+    for (long long u = threadIdx.x; u < tot; u += blockDim.x) {
+      const int pl = a.rplanes[u / a.nxy];
+      const CT v = x[(long long)pl * a.nxy + (u % a.nxy)];
+      const double vx = (double)v.x, vy = (double)v.y;
+      s += a.gr[pl] * (vx * vx + vy * vy);
+    }
+    acc[h] = s;
+  }
+  block_sum<2>(acc, red);
+  if (threadIdx.x == 0) {
+    const int item = st->item;
+    const double glj = a.gl[st->j / a.nxy];
+    double t0 = 4.0 * glj * acc[0];
+    double t1 = a.H == 2 ? 4.0 * glj * acc[1] : t0;
+    if (st->result != kOK) {
+      t0 = __longlong_as_double(0x7ff8000000000000LL);
+      t1 = t0;
+    }
+    a.res_t[item] = t0;
+    if (a.res_tm) a.res_tm[item] = t1;
+    if (a.res_it) a.res_it[item] = st->it;
+    if (a.res_status) a.res_status[item] = st->result;
+    st->status = SLOT_IDLE;
+    st->item = -1;
+    atomicAdd(&a.queue->harvested, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// work assignment (single block, deterministic slot order)
+// ---------------------------------------------------------------------------------
+
+struct AssignArgs {
+  Slot* slots;
+  int S, H;
+  Queue* queue;
+  const double* item_e;
+  const int* item_ik;
+  const long long* item_col;
+  const int* lplanes;   // planes with Gamma_L > 0
+  int nlp, nk;
+  long long nxy;
+};
+
+static __global__ void __launch_bounds__(1024) k_assign(const AssignArgs a) {
+  __shared__ int s_next, s_tot;
+  __shared__ int s_warp[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (tid == 0) s_next = a.queue->next;
+  __syncthreads();
+  const int nitems = a.queue->nitems;
+  const long long nrhs = (long long)a.nlp * a.nxy;
+  for (int base = 0; base < a.S; base += blockDim.x) {
+    const int s = base + tid;
+    int need = 0;
+    if (s < a.S) {
+      a.slots[s].init = 0;
+      need = a.slots[s].status == SLOT_IDLE;
+    }
+    // block exclusive scan of need
+    unsigned m = __ballot_sync(0xffffffffu, need);
+    int wrank = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) s_warp[wid] = __popc(m);
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        int c = s_warp[w];
+        s_warp[w] = acc;
+        acc += c;
+      }
+      s_tot = acc;
+    }
+    __syncthreads();
+    const int item = s_next + s_warp[wid] + wrank;
+    if (need && item < nitems) {
+      Slot* st = a.slots + s;
+      const double e = a.item_e[item];
+      const int ik = a.item_ik[item];
+      const long long col = a.item_col[item];
+      st->item = item;
+      st->it = 0;
+      st->refresh = 0;
+      st->rmax = 1.0;
+      st->res = 1.0;
+      st->beta = make_double2(0.0, 0.0);
+      st->rho = make_double2(a.H == 2 ? 2.0 : 1.0, 0.0);  // <e_j, e_j> in the pairing form
+      if (!isfinite(e) || ik < 0 || ik >= a.nk || col < 0 || col >= nrhs) {
+        st->ik = 0;
+        st->e = 0.0;
+        st->j = 0;
+        st->result = kEINVAL;
+        st->status = SLOT_DONE;
+      } else {
+        st->ik = ik;
+        st->e = e;
+        st->j = (long long)a.lplanes[col / a.nxy] * a.nxy + col % a.nxy;
+        st->result = 0;
+        st->status = SLOT_ACTIVE;
+        st->init = 1;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) s_next = min(s_next + s_tot, nitems);
+    __syncthreads();
+  }
+  if (tid == 0) a.queue->next = s_next;
+}
+
+// ---------------------------------------------------------------------------------
+// vector initialisation of newly assigned slots: x = 0, r = e_j, p = 0
+// ---------------------------------------------------------------------------------
+
+template <typename T>
+struct InitArgs {
+  using CT = typename Cx<T>::type;
+  CT* x;
+  CT* r;
+  CT* p;
+  const Slot* slots;
+  long long n, slot_stride;
+  int H;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_init(const InitArgs<T> a) {
+  using CT = typename Cx<T>::type;
+  const int slot = blockIdx.y;
+  const Slot* st = a.slots + slot;
+  if (!st->init) return;
+  const long long j = st->j;
+  const long long base = (long long)slot * a.slot_stride;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    for (int h = 0; h < a.H; ++h) {
+      const long long off = base + (long long)h * a.n + i;
+      a.x[off] = czero<CT>();
+      a.p[off] = czero<CT>();
+      CT rv = czero<CT>();
+      if (i == j) rv.x = (T)1;
+      a.r[off] = rv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// stand-alone trace of given vectors (checks the reduction on its own)
+// ---------------------------------------------------------------------------------
+
+struct VecTraceArgs {
+  const double2* x;  // [v][n]
+  const long long* cols;
+  const int* lplanes;
+  const int* rplanes;
+  int nlp, nrp;
+  const double* gl;
+  const double* gr;
+  double* t_out;
+  long long nxy, n;
+};
+
+static __global__ void __launch_bounds__(256) k_vec_trace(const VecTraceArgs a) {
+  __shared__ double red[1][32];
+  const int v = blockIdx.x;
+  const double2* x = a.x + (long long)v * a.n;
+  const long long tot = (long long)a.nrp * a.nxy;
+  double s[1] = {0.0};
+  for (long long u = threadIdx.x; u < tot; u += blockDim.x) {
+    const int pl = a.rplanes[u / a.nxy];
+    const double2 val = x[(long long)pl * a.nxy + (u % a.nxy)];
+    s[0] += a.gr[pl] * (val.x * val.x + val.y * val.y);
+  }
+  block_sum<1>(s, red);
+  if (threadIdx.x == 0) {
+    const long long col = a.cols[v];
+    const long long nrhs = (long long)a.nlp * a.nxy;
+    if (col < 0 || col >= nrhs) {
+      a.t_out[v] = __longlong_as_double(0x7ff8000000000000LL);
+    } else {
+      const int pl = a.lplanes[col / a.nxy];
+      a.t_out[v] = 4.0 * a.gl[pl] * s[0];
+    }
+  }
+}
+
+}  // namespace transec
