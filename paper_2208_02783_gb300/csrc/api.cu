@@ -366,13 +366,13 @@ int run_plain(transec_ctx* ctx, int H, int nitems, const double* d_e, const int*
   for (int i = 0; i < C; ++i) {
     sa.p_in = (i % 2 == 0) ? eng.P0 : eng.P1;
     sa.p_out = (i % 2 == 0) ? eng.P1 : eng.P0;
-    if (prof) cudaEventRecord(ctx->prof_ev[4 * i + 0], s);
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 0], s, cudaEventRecordExternal);
     launch_stencil<T>(ctx->g.R, sg, eng.threads, eng.smem, s, sa);
-    if (prof) cudaEventRecord(ctx->prof_ev[4 * i + 1], s);
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 1], s, cudaEventRecordExternal);
     ua.p = sa.p_out;
-    if (prof) cudaEventRecord(ctx->prof_ev[4 * i + 2], s);
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 2], s, cudaEventRecordExternal);
     k_update<T><<<ug, 256, 0, s>>>(ua);
-    if (prof) cudaEventRecord(ctx->prof_ev[4 * i + 3], s);
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 3], s, cudaEventRecordExternal);
     k_scalars<<<cgrid, 256, 0, s>>>(ca);
   }
   k_trace<T><<<aa.S, 256, 0, s>>>(ta);
