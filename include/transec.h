@@ -171,6 +171,25 @@ int transec_apply(transec_ctx* ctx, double energy, int ik, int conj_k, int nvec,
                   const double* x, double* y, int on_device);
 
 /*
+ * Operator apply that allocates nothing (the paper has no counterpart: this is a
+ * library service).  For callers that may not have the library call cudaMalloc or
+ * cudaFree -- a process whose device memory is owned by another allocator, or a
+ * latency-critical loop that cannot take cudaFree's implicit synchronisation --
+ * this computes the same y_v = A(E, k_ik) x_v (A(E, -k) if conj_k != 0) as
+ * transec_apply, for nvec complex128 vectors in grid order, with x and y DEVICE
+ * pointers on the context's device.  The stencil's scratch lives in a fixed static
+ * device array of about 17 MiB that every GPU loading the library holds until exit;
+ * limits: nvec <= 64 and nvec * nx * ny * nz <= 1048576 (EINVAL beyond them, with a
+ * message naming the limit).  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the GPU
+ * race, so issue them one after another.  The context itself is created (and its
+ * buffers allocated) beforehand by transec_create / transec_set_*.
+ */
+int transec_apply_noalloc(transec_ctx* ctx, double energy, int ik, int conj_k, int nvec,
+                          const double* x, double* y);
+
+/*
  * Column trace (the reduction on its own): for nvec solution vectors x_v (complex128,
  * grid order, one after another) and left-CAP column positions cols[v], write
  * t_out[v] = 4 Gamma_L(j_v) sum_i Gamma_R(i) |x_v(i)|^2.  Device or host memory.

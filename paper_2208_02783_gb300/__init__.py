@@ -12,7 +12,7 @@ import numpy as np
 from .binding import (  # noqa: F401
     EBREAKDOWN, ECUDA, EINVAL, ENOCONV, ENOMEM, ESTATE, ETIMEOUT, METHOD_AUTO, METHOD_BICG,
     METHOD_COCG, OK, PREC_FP64, PREC_MIXED, SolverOpts, TransecError, load,
-    transec_apply, transec_column_contributions, transec_create, transec_destroy,
+    transec_apply, transec_apply_noalloc, transec_column_contributions, transec_create, transec_destroy,
     transec_get_solver, transec_last_error, transec_n_rhs, transec_set_abc,
     transec_set_kmesh, transec_set_potential, transec_set_solver, transec_stats,
     transec_stats_reset, transec_status_string, transec_trace, transec_transmission,

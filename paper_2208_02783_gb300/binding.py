@@ -68,6 +68,7 @@ _SIGS = {
     "transec_transmission": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "transec_column_contributions": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int]),
     "transec_apply": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int]),
+    "transec_apply_noalloc": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _P, _P]),
     "transec_trace": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
     "transec_stats": (C.c_int, [_P] + [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double), C.POINTER(C.c_longlong),
@@ -265,6 +266,19 @@ def transec_apply(ctx, energy, ik, x, y, conj_k=False):
     nvec = n_el // (2 * g)
     st = load().transec_apply(ctx, float(energy), int(ik), 1 if conj_k else 0, nvec, a.ptr, b.ptr, side)
     return _check(ctx, st, "transec_apply")
+
+
+def transec_apply_noalloc(ctx, energy, ik, x, y, conj_k=False):
+    """y = A(E, k) x with no device allocation; x and y must be CUDA tensors."""
+    xv = _complex_view(x)
+    yv = _complex_view(y)
+    a = _Arr(xv, np.float64)
+    b = _Arr(yv, np.float64, writable=True)
+    if _side([a, b]) != 1:
+        raise ValueError("transec_apply_noalloc takes device (CUDA) tensors")
+    nvec = int(a.keep.numel()) // (2 * transec_n_points(ctx))
+    st = load().transec_apply_noalloc(ctx, float(energy), int(ik), 1 if conj_k else 0, nvec, a.ptr, b.ptr)
+    return _check(ctx, st, "transec_apply_noalloc")
 
 
 def transec_trace(ctx, x, cols, t_out):
