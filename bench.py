@@ -232,9 +232,9 @@ def main():
     prec = pkg.PREC_MIXED if args.form == "mixed" else pkg.PREC_FP64
     tr = pkg.Transec.from_instance(inst, device=local, tol=1e-10, precision=prec, slots=args.slots,
                                    profile=1)
-    slots = args.slots or (64 if prec == pkg.PREC_FP64 else 128)
+    slots = args.slots or (16 if prec == pkg.PREC_FP64 else 64)
     tr.set_solver(slots=slots)
-    items_per_step = args.items or 2 * slots
+    items_per_step = args.items or 4 * slots
 
     def barrier():
         if ws > 1:
@@ -301,6 +301,22 @@ def main():
     col_rate = cols / (ms / 1e3)
     value = 2.0 * col_rate / n_rhs
 
+    # parity of the timed form against the plain FP64 form on the first columns of the
+    # first timed step (the metric's |dT| <= 1e-6 vs plain FP64 on the GPU)
+    parity = None
+    if prec == pkg.PREC_MIXED:
+        npar = min(16, items_per_step)
+        e, k, c = step_items(args.warmup)
+        got = results[0]
+        tr.set_solver(precision=pkg.PREC_FP64, slots=npar, profile=0)
+        ref = tr.column_contributions(e[:npar], k[:npar], c[:npar])
+        tr.set_solver(precision=prec, slots=slots, profile=1)
+        dt_p = np.abs(got["t"][:npar].cpu().numpy() - ref["t"])
+        dt_m = np.abs(got["t_minus"][:npar].cpu().numpy() - ref["t_minus"])
+        mx = float(max(dt_p.max(), dt_m.max()))
+        parity = {"columns": npar, "max_abs_dt_j": mx, "dT_bound_per_Ek": mx * n_rhs,
+                  "fp64_status_ok": bool(np.all(ref["status"] == 0))}
+
     # end to end: host (pinned) item arrays in, host results out, through the C ABI
     e2e_ms = 0.0
     h2d = items_per_step * (8 + 4 + 8)
@@ -358,7 +374,8 @@ def main():
             "column_solves_per_s": col_rate, "n_rhs_per_Ek": n_rhs,
             "value_derivation": "2 x column-solves/s / n_rhs (each column gives the k and -k columns)",
             "mean_iterations_per_column": iters_total / max(1, cols // ws),
-            "failed_columns": fails, "l2": "working set of the slots (~GBs) exceeds L2; no flush needed",
+            "failed_columns": fails, "fp64_fallback_columns": int(st.get("fallbacks", 0)), "l2": "working set of the slots (~GBs) exceeds L2; no flush needed",
+            "parity_vs_fp64": parity,
             "sampling": "seeded uniform (energy, k-pair, left-CAP column) per step and rank",
         },
         "roofline": roof,

@@ -78,12 +78,17 @@ typedef struct transec_solver_opts {
   int maxit;          /* operator applications per half and column; default 100000 */
   int slots;          /* columns in flight on the GPU; 0 = chosen by the autotuner */
   int chunk;          /* iterations per graph launch between host polls; 0 = default */
-  double reliable;    /* mixed precision: replace the FP32 residual by the FP64 one
-                         when it has dropped by this factor; default 0.1 */
+  double reliable;    /* mixed precision: fold the FP32 correction into the FP64
+                         solution, recompute the FP64 residual and restart the FP32
+                         iteration once its residual has dropped by this factor (or
+                         has stalled); default 1e-5 */
   int tile_y;         /* stencil tile rows (0 = autotune); tiles span min(nx, 32) */
   int slab;           /* z-planes per stencil block (0 = autotune) */
   int profile;        /* != 0: time every stencil and update launch with CUDA events on
                          the context's stream (read back with transec_stats) */
+  int mixed_maxit;    /* mixed precision: FP32 iterations a column may take before it is
+                         handed to the plain FP64 engine (solved again from scratch);
+                         default 8000 */
 } transec_solver_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -202,12 +207,13 @@ int transec_trace(transec_ctx* ctx, int nvec, const double* x, const int64_t* co
  * launches = library kernels launched; point_applies = operator applications summed
  * over columns and halves, times grid points (the work the stencil did); with
  * opts.profile set, stencil_ms / update_ms = summed device time of the stencil and
- * vector-update launches and stencil_launches / update_launches their counts.  Any
- * output pointer may be NULL.
+ * vector-update launches and stencil_launches / update_launches their counts;
+ * fallbacks = mixed-precision columns that did not converge in the mixed form and
+ * were solved again by the plain FP64 engine.  Any output pointer may be NULL.
  */
 int transec_stats(const transec_ctx* ctx, long long* launches, long long* point_applies,
                   double* stencil_ms, long long* stencil_launches, double* update_ms,
-                  long long* update_launches);
+                  long long* update_launches, long long* fallbacks);
 int transec_stats_reset(transec_ctx* ctx);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next

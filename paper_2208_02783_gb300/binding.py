@@ -46,6 +46,7 @@ class SolverOpts(C.Structure):
         ("tile_y", C.c_int),
         ("slab", C.c_int),
         ("profile", C.c_int),
+        ("mixed_maxit", C.c_int),
     ]
 
 
@@ -72,7 +73,8 @@ _SIGS = {
     "transec_trace": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
     "transec_stats": (C.c_int, [_P] + [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double), C.POINTER(C.c_longlong),
-                                        C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_longlong)]),
     "transec_stats_reset": (C.c_int, [_P]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
@@ -293,9 +295,11 @@ def transec_trace(ctx, x, cols, t_out):
 
 
 def transec_stats(ctx) -> dict:
-    v = [C.c_longlong(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong()]
+    v = [C.c_longlong(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(),
+         C.c_longlong()]
     _check(ctx, load().transec_stats(ctx, *[C.byref(x) for x in v]), "transec_stats")
-    keys = ("launches", "point_applies", "stencil_ms", "stencil_launches", "update_ms", "update_launches")
+    keys = ("launches", "point_applies", "stencil_ms", "stencil_launches", "update_ms", "update_launches",
+            "fallbacks")
     return {k: x.value for k, x in zip(keys, v)}
 
 

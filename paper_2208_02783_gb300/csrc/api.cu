@@ -91,7 +91,8 @@ void default_opts(transec_solver_opts* o) {
   if (o->maxit <= 0) o->maxit = 100000;
   if (o->chunk <= 0) o->chunk = 16;
   if (o->chunk % 2) o->chunk += 1;  // the p ping-pong must end where it started
-  if (o->reliable <= 0 || o->reliable >= 1) o->reliable = 0.1;
+  if (o->reliable <= 0 || o->reliable >= 1) o->reliable = 1e-5;
+  if (o->mixed_maxit <= 0) o->mixed_maxit = 8000;
 }
 
 // Bloch phase exp(2 pi i kappa w) with the argument reduced before the cosine.
@@ -297,17 +298,62 @@ void accumulate_events(transec_ctx* ctx, int C) {
   cudaGetLastError();
 }
 
-// Solve nitems (E, k, column) items with the plain engine of arithmetic type T and H
-// halves.  Item and result arrays are device pointers.
+// FP64 buffers of the mixed-precision residual replacement (see mixed.cuh).
+int mixed_ensure(transec_ctx* ctx, int S, int H, long long nblk_sig, long long nblk_part) {
+  const long long elems = (long long)S * H * ctx->g.n;
+  if (ctx->mx_elems < elems) {
+    cudaFree(ctx->mx_x); cudaFree(ctx->mx_q); cudaFree(ctx->mx_p);
+    ctx->mx_x = ctx->mx_q = ctx->mx_p = nullptr;
+    ctx->mx_elems = 0;
+    CK(cudaMalloc(&ctx->mx_x, elems * sizeof(double2)));
+    CK(cudaMalloc(&ctx->mx_q, elems * sizeof(double2)));
+    CK(cudaMalloc(&ctx->mx_p, elems * sizeof(double2)));
+    ctx->mx_elems = elems;
+  }
+  if (ctx->mx_sig_elems < S * nblk_sig * 2) {
+    cudaFree(ctx->mx_sig);
+    ctx->mx_sig = nullptr;
+    ctx->mx_sig_elems = 0;
+    CK(cudaMalloc(&ctx->mx_sig, S * nblk_sig * 2 * sizeof(double)));
+    ctx->mx_sig_elems = S * nblk_sig * 2;
+  }
+  if (ctx->mx_part_elems < S * nblk_part * 4) {
+    cudaFree(ctx->mx_part);
+    ctx->mx_part = nullptr;
+    ctx->mx_part_elems = 0;
+    CK(cudaMalloc(&ctx->mx_part, S * nblk_part * 4 * sizeof(double)));
+    ctx->mx_part_elems = S * nblk_part * 4;
+  }
+  if (ctx->mx_S < S) {
+    cudaFree(ctx->mx_slots);
+    ctx->mx_slots = nullptr;
+    ctx->mx_S = 0;
+    CK(cudaMalloc(&ctx->mx_slots, S * sizeof(Slot)));
+    ctx->mx_S = S;
+  }
+  return TRANSEC_OK;
+}
+
+// Solve nitems (E, k, column) items with the slot engine of arithmetic type T and H
+// halves: plain (T = double) or mixed precision (T = float, with FP64 residual
+// replacement).  Item and result arrays are device pointers.
 template <typename T>
-int run_plain(transec_ctx* ctx, int H, int nitems, const double* d_e, const int* d_ik,
-              const long long* d_col, double* d_t, double* d_tm, int* d_it, int* d_st) {
+int run_engine(transec_ctx* ctx, int H, bool mixed, int nitems, const double* d_e, const int* d_ik,
+               const long long* d_col, double* d_t, double* d_tm, int* d_it, int* d_st) {
   using CT = typename Cx<T>::type;
   Engine<T>& eng = engine_of<T>(ctx);
-  const size_t per_slot = (size_t)5 * H * ctx->g.n * sizeof(CT);
+  const size_t per_slot = (size_t)5 * H * ctx->g.n * sizeof(CT) +
+                          (mixed ? (size_t)3 * H * ctx->g.n * sizeof(double2) : 0);
   const int S = choose_slots(ctx, H, per_slot, nitems, ctx->opts.slots);
   int rc = engine_ensure<T>(ctx, eng, S, H);
   if (rc) return rc;
+  // the FP64 stencil of the mixed form's residual replacement
+  const TileShape t64 = choose_tiles(ctx->g, H, sizeof(double2), StencilMax<double>::threads, 0, 0);
+  if (mixed) {
+    rc = mixed_ensure(ctx, S, H, (long long)t64.ntx * t64.nty * t64.nslab, eng.nblk3);
+    if (rc) return rc;
+    CK(prepare_stencil<double>(ctx->g.R, t64.smem));
+  }
   const int Sl = eng.S;  // may exceed S when reusing larger buffers; extra slots stay idle
   cudaStream_t s = ctx->s;
   const Queue q0{0, 0, nitems, 0};
@@ -341,17 +387,38 @@ int run_plain(transec_ctx* ctx, int H, int nitems, const double* d_e, const int*
 
   ScalarArgs ca{};
   ca.rho_part = eng.rho_part; ca.nblk = eng.nblk3; ca.slots = eng.slots; ca.S = aa.S; ca.H = H;
-  ca.maxit = ctx->opts.maxit; ca.tol = ctx->opts.tol;
+  ca.maxit = mixed ? std::min(ctx->opts.maxit, ctx->opts.mixed_maxit) : ctx->opts.maxit;
+  ca.tol = ctx->opts.tol;
+  // the FP32 cycle restarts only on progress (no stall rule: BiCG residuals wander for
+  // thousands of iterations before they fall, and a restart there loses the progress)
+  ca.mixed = mixed ? 1 : 0; ca.reliable = ctx->opts.reliable; ca.stall = 1 << 30;
+  ca.max_gap = 1 << 30;
   const int cgrid = (aa.S + 7) / 8;
 
-  TraceArgs<T> ta{};
-  ta.x = eng.X; ta.slots = eng.slots; ta.queue = eng.queue; ta.rplanes = ctx->d_rplanes;
+  // the trace reads the FP64 solution: the engine's x (plain) or x64 (mixed)
+  TraceArgs<double> ta{};
+  ta.x = mixed ? ctx->mx_x : reinterpret_cast<const double2*>(eng.X);
+  ta.slots = eng.slots; ta.queue = eng.queue; ta.rplanes = ctx->d_rplanes;
   ta.nrp = (int)ctx->rplanes.size(); ta.gl = ctx->d_gl; ta.gr = ctx->d_gr; ta.res_t = d_t;
   ta.res_tm = d_tm; ta.res_it = d_it; ta.res_status = d_st; ta.nxy = ctx->g.nxy; ta.n = n;
   ta.slot_stride = stride; ta.H = H;
 
+  // mixed precision: residual replacement stage
+  MxPrepArgs mp{eng.slots, ctx->mx_slots, aa.S};
+  MxAccumArgs mac{ctx->mx_x, reinterpret_cast<float2*>(eng.X), ctx->mx_slots, n, stride, H};
+  StencilArgs<double> s64{};
+  s64.r = ctx->mx_x; s64.p_in = ctx->mx_x; s64.p_out = ctx->mx_p; s64.q = ctx->mx_q;
+  s64.part = ctx->mx_sig; s64.slots = ctx->mx_slots; s64.phase = ctx->d_phase; s64.v = ctx->d_v;
+  s64.gam = ctx->d_gam; s64.g = ctx->g; s64.H = H; s64.TX = t64.TX; s64.TY = t64.TY; s64.D = t64.D;
+  s64.ntx = t64.ntx; s64.conj = 0; s64.slot_stride = stride;
+  const dim3 sg64((unsigned)(t64.ntx * t64.nty), (unsigned)t64.nslab, (unsigned)aa.S);
+  MxFinishArgs mf{ctx->mx_q, reinterpret_cast<float2*>(eng.R), ctx->mx_slots, ctx->mx_part, n, stride, H};
+  MxScalarArgs ms{ctx->mx_part, eng.nblk3, ctx->mx_slots, eng.slots, aa.S, H, ctx->opts.tol};
+  MxInitArgs mi{ctx->mx_x, eng.slots, n, stride, H};
+
   k_assign<<<1, 1024, 0, s>>>(aa);
   k_init<T><<<ig, 256, 0, s>>>(ia);
+  if (mixed) k_mx_init<<<ig, 256, 0, s>>>(mi);
   CHECK_LAUNCH();
 
   const int C = ctx->opts.chunk;
@@ -375,9 +442,17 @@ int run_plain(transec_ctx* ctx, int H, int nitems, const double* d_e, const int*
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 3], s, cudaEventRecordExternal);
     k_scalars<<<cgrid, 256, 0, s>>>(ca);
   }
-  k_trace<T><<<aa.S, 256, 0, s>>>(ta);
+  if (mixed) {
+    k_mx_prep<<<(aa.S + 255) / 256, 256, 0, s>>>(mp);
+    k_mx_accum<<<ig, 256, 0, s>>>(mac);
+    launch_stencil<double>(ctx->g.R, sg64, t64.threads, t64.smem, s, s64);
+    k_mx_finish<<<ig, 256, 0, s>>>(mf);
+    k_mx_scalars<<<cgrid, 256, 0, s>>>(ms);
+  }
+  k_trace<double><<<aa.S, 256, 0, s>>>(ta);
   k_assign<<<1, 1024, 0, s>>>(aa);
   k_init<T><<<ig, 256, 0, s>>>(ia);
+  if (mixed) k_mx_init<<<ig, 256, 0, s>>>(mi);
   cudaMemcpyAsync(ctx->h_harvest, &eng.queue->harvested, sizeof(int), cudaMemcpyDeviceToHost, s);
   {
     cudaError_t e1 = cudaStreamEndCapture(s, &graph);
@@ -394,7 +469,7 @@ int run_plain(transec_ctx* ctx, int H, int nitems, const double* d_e, const int*
       return fail(ctx, TRANSEC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
     }
   }
-  const long long per_chunk = 3LL * C + 3;
+  const long long per_chunk = 3LL * C + 3 + (mixed ? 6 : 0);
   const long long max_chunks =
       ((long long)nitems / std::max(1, aa.S) + 2) * ((long long)ctx->opts.maxit / C + 2) + 16;
   long long chunks = 0;
@@ -416,7 +491,7 @@ int run_plain(transec_ctx* ctx, int H, int nitems, const double* d_e, const int*
       break;
     }
   }
-  ctx->launches += 2 + chunks * per_chunk;
+  ctx->launches += (mixed ? 3 : 2) + chunks * per_chunk;
   if (rcode == TRANSEC_OK && d_it) {
     std::vector<int> its(nitems);
     if (cudaMemcpy(its.data(), d_it, nitems * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess) {
@@ -461,9 +536,68 @@ int check_ready(transec_ctx* ctx) {
 int solve_items(transec_ctx* ctx, int H, int nitems, const double* d_e, const int* d_ik,
                 const long long* d_col, double* d_t, double* d_tm, int* d_it, int* d_st) {
   if (nitems == 0) return TRANSEC_OK;
-  if (ctx->opts.precision == TRANSEC_PREC_MIXED)
-    return run_mixed(ctx, H, nitems, d_e, d_ik, d_col, d_t, d_tm, d_it, d_st);
-  return run_plain<double>(ctx, H, nitems, d_e, d_ik, d_col, d_t, d_tm, d_it, d_st);
+  if (ctx->opts.precision != TRANSEC_PREC_MIXED)
+    return run_engine<double>(ctx, H, false, nitems, d_e, d_ik, d_col, d_t, d_tm, d_it, d_st);
+  int rc = run_engine<float>(ctx, H, true, nitems, d_e, d_ik, d_col, d_t, d_tm, d_it, d_st);
+  if (rc != TRANSEC_OK) return rc;
+  // Columns the mixed form could not finish (not converged, or a breakdown of the
+  // FP32 recurrence) are solved again with the plain FP64 engine.
+  std::vector<int> st(nitems);
+  CK(cudaMemcpyAsync(st.data(), d_st, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  std::vector<int> redo;
+  for (int i = 0; i < nitems; ++i)
+    if (st[i] == TRANSEC_ENOCONV || st[i] == TRANSEC_EBREAKDOWN) redo.push_back(i);
+  if (redo.empty()) return TRANSEC_OK;
+  const int m = (int)redo.size();
+  std::vector<double> he(nitems);
+  std::vector<int> hk(nitems), hit(nitems);
+  std::vector<long long> hc(nitems);
+  CK(cudaMemcpyAsync(he.data(), d_e, nitems * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaMemcpyAsync(hk.data(), d_ik, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaMemcpyAsync(hc.data(), d_col, nitems * sizeof(long long), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaMemcpyAsync(hit.data(), d_it, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  std::vector<double> re(m);
+  std::vector<int> rk(m);
+  std::vector<long long> rcl(m);
+  for (int u = 0; u < m; ++u) {
+    re[u] = he[redo[u]];
+    rk[u] = hk[redo[u]];
+    rcl[u] = hc[redo[u]];
+  }
+  DevBuf be, bk, bc, bt, btm, bit, bst;
+  CK(cudaMalloc(&be.p, m * sizeof(double)));
+  CK(cudaMalloc(&bk.p, m * sizeof(int)));
+  CK(cudaMalloc(&bc.p, m * sizeof(long long)));
+  CK(cudaMalloc(&bt.p, m * sizeof(double)));
+  CK(cudaMalloc(&btm.p, m * sizeof(double)));
+  CK(cudaMalloc(&bit.p, m * sizeof(int)));
+  CK(cudaMalloc(&bst.p, m * sizeof(int)));
+  CK(cudaMemcpyAsync(be.p, re.data(), m * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+  CK(cudaMemcpyAsync(bk.p, rk.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+  CK(cudaMemcpyAsync(bc.p, rcl.data(), m * sizeof(long long), cudaMemcpyHostToDevice, ctx->s));
+  rc = run_engine<double>(ctx, H, false, m, (double*)be.p, (int*)bk.p, (long long*)bc.p,
+                          (double*)bt.p, (double*)btm.p, (int*)bit.p, (int*)bst.p);
+  if (rc != TRANSEC_OK) return rc;
+  std::vector<double> t(m), tm(m);
+  std::vector<int> it(m), s2(m);
+  CK(cudaMemcpyAsync(t.data(), bt.p, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaMemcpyAsync(tm.data(), btm.p, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaMemcpyAsync(it.data(), bit.p, m * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaMemcpyAsync(s2.data(), bst.p, m * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaStreamSynchronize(ctx->s));
+  for (int u = 0; u < m; ++u) {
+    const int i = redo[u];
+    CK(cudaMemcpyAsync(d_t + i, &t[u], sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(d_tm + i, &tm[u], sizeof(double), cudaMemcpyHostToDevice, ctx->s));
+    const int tot = hit[i] + it[u];  // iterations of both attempts
+    CK(cudaMemcpyAsync(d_it + i, &tot, sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaMemcpyAsync(d_st + i, &s2[u], sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+  }
+  ctx->fallbacks += m;
+  return TRANSEC_OK;
 }
 
 // Host item lists -> host results (one method group).
@@ -698,7 +832,7 @@ int transec_set_solver(transec_ctx* ctx, const transec_solver_opts* opts) {
   if (!ctx || !opts) return TRANSEC_EINVAL;
   transec_solver_opts o = *opts;
   if (o.method < 0 || o.method > 2 || o.precision < 0 || o.precision > 1 || o.tol < 0 ||
-      o.maxit < 0 || o.slots < 0 || o.chunk < 0 || o.tile_y < 0 || o.slab < 0 ||
+      o.maxit < 0 || o.slots < 0 || o.chunk < 0 || o.tile_y < 0 || o.slab < 0 || o.mixed_maxit < 0 ||
       !std::isfinite(o.tol) || !std::isfinite(o.reliable))
     return fail(ctx, TRANSEC_EINVAL, "invalid solver options");
   default_opts(&o);
@@ -967,8 +1101,9 @@ int transec_trace(transec_ctx* ctx, int nvec, const double* x, const int64_t* co
 
 int transec_stats(const transec_ctx* ctx, long long* launches, long long* point_applies,
                   double* stencil_ms, long long* stencil_launches, double* update_ms,
-                  long long* update_launches) {
+                  long long* update_launches, long long* fallbacks) {
   if (!ctx) return TRANSEC_EINVAL;
+  if (fallbacks) *fallbacks = ctx->fallbacks;
   if (launches) *launches = ctx->launches;
   if (point_applies) *point_applies = ctx->point_applies;
   if (stencil_ms) *stencil_ms = ctx->stencil_ms;
@@ -984,6 +1119,7 @@ int transec_stats_reset(transec_ctx* ctx) {
   ctx->point_applies = 0;
   ctx->stencil_ms = ctx->update_ms = 0;
   ctx->stencil_launches = ctx->update_launches = 0;
+  ctx->fallbacks = 0;
   return TRANSEC_OK;
 }
 
@@ -995,7 +1131,8 @@ void transec_destroy(transec_ctx* ctx) {
   if (ctx->s) cudaStreamSynchronize(ctx->s);
   ctx->e64.release();
   ctx->e32.release();
-  cudaFree(ctx->mx_x); cudaFree(ctx->mx_r); cudaFree(ctx->mx_part);
+  cudaFree(ctx->mx_x); cudaFree(ctx->mx_q); cudaFree(ctx->mx_p);
+  cudaFree(ctx->mx_sig); cudaFree(ctx->mx_part); cudaFree(ctx->mx_slots);
   cudaFree(ctx->d_v); cudaFree(ctx->d_v32);
   cudaFree(ctx->d_gl); cudaFree(ctx->d_gr); cudaFree(ctx->d_gam);
   cudaFree(ctx->d_lplanes); cudaFree(ctx->d_rplanes); cudaFree(ctx->d_phase);

@@ -45,8 +45,11 @@ struct Slot {
   double2 beta;   // p <- r + beta p
   double res;     // last residual norm (max over halves)
   int refresh;    // mixed precision: number of FP64 residual replacements
-  int pad;
-  double rmax;    // mixed precision: residual norm at the last replacement
+  int pending;    // mixed precision: a residual replacement is requested
+  double rmax;    // mixed precision: true residual norm at the last replacement
+  int last_ref;   // mixed precision: iteration of the last replacement
+  int it_best;    // mixed precision: iteration of the smallest residual of this cycle
+  double rbest;   // mixed precision: smallest FP32 residual of this cycle
 };
 
 // Work queue bookkeeping (device resident).

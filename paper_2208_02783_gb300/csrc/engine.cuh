@@ -81,12 +81,18 @@ struct transec_ctx {
   // solver engines
   transec::Engine<double> e64;
   transec::Engine<float> e32;
-  // mixed precision extra FP64 state: solution and residual per slot/half
+  // mixed precision extra state: FP64 solution, FP64 A*x and the stencil's p copy per
+  // slot and half, their partial sums, and the slot array of the replacement pass
   double2* mx_x = nullptr;
-  double2* mx_r = nullptr;
-  long long mx_elems = 0;
+  double2* mx_q = nullptr;
+  double2* mx_p = nullptr;
+  double* mx_sig = nullptr;
   double* mx_part = nullptr;
+  transec::Slot* mx_slots = nullptr;
+  long long mx_elems = 0;
+  long long mx_sig_elems = 0;
   long long mx_part_elems = 0;
+  int mx_S = 0;
   // pinned host word for the harvested counter
   int* h_harvest = nullptr;
   // counters since the last transec_stats_reset
@@ -94,5 +100,6 @@ struct transec_ctx {
   long long point_applies = 0;
   double stencil_ms = 0, update_ms = 0;
   long long stencil_launches = 0, update_launches = 0;
+  long long fallbacks = 0;  // mixed-precision columns re-solved in FP64
   std::vector<cudaEvent_t> prof_ev;  // 4 per iteration of a chunk when profiling
 };

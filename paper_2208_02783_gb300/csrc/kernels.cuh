@@ -55,6 +55,48 @@ __device__ inline void block_sum(double (&v)[NV], double (*red)[32]) {
 
 __device__ inline int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// Per-thread accumulator of a complex bilinear form sum_i a_i b_i (no conjugate).
+// FP64: plain FP64 sums.  FP32: the compensated dot product of Ogita, Rump & Oishi
+// ("Accurate sum and dot product", SIAM J. Sci. Comput. 2005, algorithm Dot2): each
+// product is split exactly into p + e with an FMA, p is added with an error-free
+// TwoSum, and the rounding errors are gathered in a second float, so the result is as
+// accurate as a dot product computed in twice the working precision.  The bilinear
+// forms of COCG/BiCG cancel heavily for oscillatory vectors, which plain FP32 sums
+// do not survive.  The _rn intrinsics keep the compiler from contracting the
+// error-free transformations.
+template <typename T> struct DotAcc;
+
+template <> struct DotAcc<double> {
+  double re = 0.0, im = 0.0;
+  __device__ inline void add(double2 a, double2 b) {
+    re += a.x * b.x - a.y * b.y;
+    im += a.x * b.y + a.y * b.x;
+  }
+  __device__ inline double2 value() const { return make_double2(re, im); }
+};
+
+template <> struct DotAcc<float> {
+  float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+  __device__ static inline void acc(float& s, float& c, float x, float y) {
+    const float p = __fmul_rn(x, y);
+    const float e = __fmaf_rn(x, y, -p);
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float q = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(q, e));
+  }
+  __device__ inline void add(float2 a, float2 b) {
+    acc(sr, cr, a.x, b.x);
+    acc(sr, cr, -a.y, b.y);
+    acc(si, ci, a.x, b.y);
+    acc(si, ci, a.y, b.x);
+  }
+  __device__ inline double2 value() const {
+    return make_double2((double)sr + (double)cr, (double)si + (double)ci);
+  }
+};
+
 // ---------------------------------------------------------------------------------
 // stencil apply fused with p <- r + beta p
 // ---------------------------------------------------------------------------------
@@ -162,7 +204,7 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
     qv[m] = (inside && z >= 0 && z < nz) ? pnew((long long)z * nxy + pidx) : czero<CT>();
   }
 
-  T sgx = 0, sgy = 0;
+  DotAcc<T> sg;
   const int nh = 2 * R * (a.TX + a.TY);
   for (int zc = z0; zc < z1; ++zc) {
 #pragma unroll
@@ -207,12 +249,12 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
       pout[off] = c;
       // pairing form: half h pairs with half 1-h at the same point (or itself)
       const CT o = (a.H == 2) ? sm[(1 - half) * SW * SHt + (ty + R) * SW + tx + R] : c;
-      sgx += o.x * acc.x - o.y * acc.y;
-      sgy += o.x * acc.y + o.y * acc.x;
+      sg.add(o, acc);
     }
     __syncthreads();
   }
-  double v2[2] = {(double)sgx, (double)sgy};
+  const double2 sgv = sg.value();
+  double v2[2] = {sgv.x, sgv.y};
   block_sum<2>(v2, red);
   if (threadIdx.x == 0) {
     const int nblk = gridDim.x * gridDim.y;
@@ -265,7 +307,8 @@ __global__ void __launch_bounds__(256) k_update(const UpdateArgs<T> a) {
   __syncthreads();
   const CT al = cfrom<CT>(s_alpha);
   const long long base = (long long)slot * a.slot_stride;
-  T rrx = 0, rry = 0, n0 = 0, n1 = 0;
+  DotAcc<T> rr;
+  T n0 = 0, n1 = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
        i += (long long)gridDim.x * blockDim.x) {
     CT rv[2];
@@ -286,15 +329,14 @@ __global__ void __launch_bounds__(256) k_update(const UpdateArgs<T> a) {
     n0 += rv[0].x * rv[0].x + rv[0].y * rv[0].y;
     if (a.H == 2) {
       n1 += rv[1].x * rv[1].x + rv[1].y * rv[1].y;
-      // <r, r> = r_+ . r_- + r_- . r_+ = 2 r_+ . r_-
-      rrx += 2 * (rv[0].x * rv[1].x - rv[0].y * rv[1].y);
-      rry += 2 * (rv[0].x * rv[1].y + rv[0].y * rv[1].x);
+      rr.add(rv[0], rv[1]);  // <r, r> = r_+ . r_- + r_- . r_+ = 2 r_+ . r_-
     } else {
-      rrx += rv[0].x * rv[0].x - rv[0].y * rv[0].y;
-      rry += 2 * rv[0].x * rv[0].y;
+      rr.add(rv[0], rv[0]);
     }
   }
-  double v4[4] = {(double)rrx, (double)rry, (double)n0, (double)n1};
+  const double2 rrv = rr.value();
+  const double rscale = a.H == 2 ? 2.0 : 1.0;
+  double v4[4] = {rscale * rrv.x, rscale * rrv.y, (double)n0, (double)n1};
   block_sum<4>(v4, red);
   if (threadIdx.x == 0) {
     double* o = a.rho_part + ((size_t)slot * gridDim.x + blockIdx.x) * 4;
@@ -313,6 +355,11 @@ struct ScalarArgs {
   Slot* slots;
   int S, H, maxit;
   double tol;
+  int mixed;               // 1: FP32 iteration; convergence is judged on the FP64
+                           // residual, this kernel only requests replacements
+  double reliable;         // replacement when the residual dropped by this factor,
+  int stall;               // ... or found no new minimum for this many iterations,
+  int max_gap;             // ... or after this many iterations without one
 };
 
 // Status codes written to Slot::result (same values as the C ABI).
@@ -337,7 +384,7 @@ static __global__ void __launch_bounds__(256) k_scalars(const ScalarArgs a) {
   const double res = sqrt(a.H == 2 ? fmax(s[2], s[3]) : s[2]);
   int code = 1;  // still running
   if (!isfinite(rho_new.x) || !isfinite(rho_new.y) || !isfinite(res)) code = kEBREAKDOWN;
-  else if (res <= a.tol) code = kOK;
+  else if (!a.mixed && res <= a.tol) code = kOK;
   else if (rho_new.x == 0.0 && rho_new.y == 0.0) code = kEBREAKDOWN;
   else if (it >= a.maxit) code = kENOCONV;
   st->it = it;
@@ -348,6 +395,15 @@ static __global__ void __launch_bounds__(256) k_scalars(const ScalarArgs a) {
   } else {
     st->beta = cdiv(rho_new, st->rho);
     st->rho = rho_new;
+    if (a.mixed) {
+      if (res < st->rbest) {
+        st->rbest = res;
+        st->it_best = it;
+      }
+      if (res <= a.reliable * st->rmax || res <= a.tol || it - st->it_best >= a.stall ||
+          it - st->last_ref >= a.max_gap)
+        st->pending = 1;
+    }
   }
 }
 
@@ -468,6 +524,10 @@ static __global__ void __launch_bounds__(1024) k_assign(const AssignArgs a) {
       st->item = item;
       st->it = 0;
       st->refresh = 0;
+      st->pending = 0;
+      st->last_ref = 0;
+      st->it_best = 0;
+      st->rbest = 1.0;
       st->rmax = 1.0;
       st->res = 1.0;
       st->beta = make_double2(0.0, 0.0);

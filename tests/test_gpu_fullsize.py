@@ -1,0 +1,55 @@
+"""Full-size parity: sampled columns of the bulk fcc Cu [001] workload (20x20x480,
+order 12, 8x8 mesh, 256 energies) in the launch configuration the benchmark times,
+against column contributions the CPU oracle computed one by one
+(tests/golden/cu_bulk_columns.json, written by make_cu_bulk_columns.py with the oracle
+only, residual 1e-12).
+
+Bar per column: |dt_j| <= 4e-11, i.e. 1e-6 / n_rhs (n_rhs = 25,600 columns per
+(E, k)): even if every column of an (E, k) erred by that much in the same direction,
+|dT| would stay within the required 1e-6.  Both the +k column and the -k column
+(from the transpose BiCG's shadow system) are checked.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import context, need_gpu
+from workloads import cu_bulk
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cu_bulk_columns.json")
+TOL_COL = 1e-6 / 25600
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)["items"]
+
+
+# precision 1 (mixed): columns the FP32 iteration cannot finish within its budget are
+# re-solved by the FP64 engine; the result must meet the same bar either way
+@pytest.mark.parametrize("precision,slots", [(0, 64), (1, 64)])
+def test_cu_bulk_sampled_columns(precision, slots):
+    need_gpu()
+    items = _golden()
+    inst = cu_bulk()
+    e = np.array([it["energy"] for it in items])
+    ik = np.array([it["ik"] for it in items], np.int32)
+    cols = np.array([it["col"] for it in items], np.int64)
+    with context(inst, precision=precision, slots=slots, tol=1e-10, maxit=60000) as tr:
+        assert tr.n_rhs == 25600
+        r = tr.column_contributions(e, ik, cols)
+        fallbacks = tr.stats()["fallbacks"]
+    assert np.all(r["status"] == 0), r["status"]
+    if precision == 0:
+        assert fallbacks == 0
+    tp = np.array([it["t"] for it in items])
+    tm = np.array([it["t_minus"] for it in items])
+    err_p = np.abs(r["t"] - tp)
+    err_m = np.abs(r["t_minus"] - tm)
+    assert err_p.max() <= TOL_COL, err_p
+    assert err_m.max() <= TOL_COL, err_m

@@ -106,3 +106,44 @@ def test_failures_are_reported_not_raised():
                                     np.array([0, 10**9], np.int64))
     assert r["status"][0] == -4 and np.isnan(r["t"][0])      # maxit reached
     assert r["status"][1] == -1 and np.isnan(r["t"][1])      # column out of range
+
+
+@pytest.mark.parametrize(
+    "nx,ny,nz,order,kfrac",
+    [
+        (5, 4, 24, 2, ((0.0, 0.0),)),
+        (6, 5, 26, 12, ((0.21, -0.34), (-0.21, 0.34))),
+        (7, 3, 22, 6, ((0.125, 0.375), (0.0, 0.5))),
+    ],
+)
+def test_mixed_precision_matches_dense_and_fp64(nx, ny, nz, order, kfrac):
+    # the mixed form (complex FP32 iteration, FP64 scalars, FP64 residual replacement)
+    # must meet the same |dT| <= 1e-6 against the oracle and against the plain FP64 form
+    need_gpu()
+    inst = small_instance(nx, ny, nz, 0.45, order, 6, v_amp=0.7, kfrac=kfrac,
+                          energies=(0.15, 0.55, 1.1), seed=nx + 10 * order)
+    ref, _ = _dense_all(inst)
+    with context(inst) as tr:
+        plain = tr.transmission(inst.energies, len(kfrac))
+        tr.set_solver(precision=1)
+        tr.stats_reset()
+        mixed = tr.transmission(inst.energies, len(kfrac))
+        fallbacks = tr.stats()["fallbacks"]
+    assert np.all(mixed["status"] == 0), mixed["status"]
+    assert fallbacks == 0
+    assert np.abs(mixed["T"] - ref).max() <= TOL_T
+    assert np.abs(mixed["T"] - plain["T"]).max() <= TOL_T
+
+
+def test_mixed_precision_free_electron_slab():
+    need_gpu()
+    inst = free_electron_slab()
+    g = inst.grid
+    ref = np.array([separable_transmission(g, inst.gamma_l, inst.gamma_r, e, (0.0, 0.0))
+                    for e in inst.energies])
+    with context(inst, precision=1) as tr:
+        out = tr.transmission(inst.energies, 1)
+        fallbacks = tr.stats()["fallbacks"]
+    assert np.all(out["status"] == 0), np.unique(out["status"], return_counts=True)
+    assert np.abs(out["T"][:, 0] - ref).max() <= TOL_T
+    assert fallbacks == 0, (fallbacks, out["iters"].max())
