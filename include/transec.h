@@ -89,6 +89,10 @@ typedef struct transec_solver_opts {
   int mixed_maxit;    /* mixed precision: FP32 iterations a column may take before it is
                          handed to the plain FP64 engine (solved again from scratch);
                          default 8000 */
+  int host_loop;      /* 0 (default): the whole solve is one CUDA-graph launch whose
+                         device-side WHILE loop runs chunk after chunk until the queue is
+                         drained (bounded by maxit); != 0: the host launches and polls one
+                         chunk graph at a time (always the case when profile != 0) */
 } transec_solver_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -136,6 +140,19 @@ int transec_set_kmesh(transec_ctx* ctx, int nk, const double* kfrac, const doubl
 int transec_set_solver(transec_ctx* ctx, const transec_solver_opts* opts);
 int transec_get_solver(const transec_ctx* ctx, transec_solver_opts* opts);
 
+/*
+ * Autotune the launch shape for this context's operator (no counterpart in the
+ * paper: a property of the GPU kernels).  For each candidate stencil tile height,
+ * z-slab depth and number of columns in flight it runs a bounded burst of Krylov
+ * iterations (maxit 32) at energy E and k index ik in the configured precision,
+ * measures the stencil and update kernels with CUDA events, and keeps the candidate
+ * with the most point-applications per second in the solver options (tile_y, slab,
+ * slots).  The chosen values are also written to the non-NULL outputs.  Counters
+ * (transec_stats) are reset afterwards.  Errors: as transec_column_contributions.
+ */
+int transec_autotune(transec_ctx* ctx, double energy, int ik, int* tile_y_out, int* slab_out,
+                     int* slots_out);
+
 /* Number of left-CAP columns (right-hand sides per (E, k)). */
 int transec_n_rhs(const transec_ctx* ctx, int64_t* n_rhs);
 
@@ -165,6 +182,23 @@ int transec_column_contributions(transec_ctx* ctx, int nitems, const double* ene
                                  const int* ik, const int64_t* cols, double* t_out,
                                  double* t_minus_out, int* iters_out, int* status_out,
                                  int on_device);
+
+/*
+ * Batched sampled columns over several operators: item i is a column of context
+ * ctxs[ictx[i]] (a cell of its own size, potential, CAPs and k-mesh), solved at energy
+ * energies[i] and k index ik[i] of that context's mesh, column cols[i] of its left-CAP
+ * support; outputs as in transec_column_contributions.  The paper computes each
+ * (k, spin) independently on separate nodes (Appendix); here independent operators
+ * of uneven size share one slot engine, so one solve keeps the GPU full across all of
+ * them.  Every context must be ready, live on the same device and use the same
+ * stencil order; the solve runs with ctxs[0]'s solver options, buffers and stream.
+ * With on_device != 0 every array is a device pointer (ictx int32).  Returns the most
+ * severe per-item status; EINVAL for mismatched contexts or an out-of-range ictx / ik.
+ */
+int transec_batch_column_contributions(int nctx, transec_ctx* const* ctxs, int nitems,
+                                       const int* ictx, const double* energies, const int* ik,
+                                       const int64_t* cols, double* t_out, double* t_minus_out,
+                                       int* iters_out, int* status_out, int on_device);
 
 /*
  * Operator apply (the hot-path stencil on its own): y_v = A(E, k_ik) x_v for nvec

@@ -12,12 +12,28 @@ import numpy as np
 from .binding import (  # noqa: F401
     EBREAKDOWN, ECUDA, EINVAL, ENOCONV, ENOMEM, ESTATE, ETIMEOUT, METHOD_AUTO, METHOD_BICG,
     METHOD_COCG, OK, PREC_FP64, PREC_MIXED, SolverOpts, TransecError, load,
-    transec_apply, transec_apply_noalloc, transec_column_contributions, transec_create, transec_destroy,
+    transec_apply, transec_apply_noalloc, transec_autotune, transec_batch_column_contributions,
+    transec_column_contributions, transec_create, transec_destroy,
     transec_get_solver, transec_last_error, transec_n_rhs, transec_set_abc,
     transec_set_kmesh, transec_set_potential, transec_set_solver, transec_stats,
     transec_stats_reset, transec_status_string, transec_trace, transec_transmission,
     transec_version,
 )
+
+
+def batch_column_contributions(contexts, ictx, energies, ik, cols):
+    """Sampled columns of several ``Transec`` contexts (cells of uneven size) in one
+    solve on the first context's device and options; host arrays in and out."""
+    energies = np.ascontiguousarray(energies, np.float64)
+    n = energies.size
+    t = np.zeros(n)
+    tm = np.zeros(n)
+    it = np.zeros(n, np.int32)
+    st = np.zeros(n, np.int32)
+    rc = transec_batch_column_contributions([c.ctx for c in contexts], np.asarray(ictx, np.int32),
+                                            energies, np.asarray(ik, np.int32),
+                                            np.asarray(cols, np.int64), t, tm, it, st)
+    return {"t": t, "t_minus": tm, "iters": it, "status": st, "rc": rc}
 
 
 class Transec:
@@ -61,6 +77,10 @@ class Transec:
     def solver(self) -> dict:
         o = transec_get_solver(self.ctx)
         return {f: getattr(o, f) for f, _ in o._fields_}
+
+    def autotune(self, energy, ik=0) -> dict:
+        """Pick tile height, slab depth and columns in flight for this operator."""
+        return transec_autotune(self.ctx, energy, ik)
 
     @property
     def n_rhs(self) -> int:

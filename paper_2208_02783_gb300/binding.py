@@ -47,6 +47,7 @@ class SolverOpts(C.Structure):
         ("slab", C.c_int),
         ("profile", C.c_int),
         ("mixed_maxit", C.c_int),
+        ("host_loop", C.c_int),
     ]
 
 
@@ -66,8 +67,12 @@ _SIGS = {
     "transec_set_solver": (C.c_int, [_P, C.POINTER(SolverOpts)]),
     "transec_get_solver": (C.c_int, [_P, C.POINTER(SolverOpts)]),
     "transec_n_rhs": (C.c_int, [_P, C.POINTER(C.c_int64)]),
+    "transec_autotune": (C.c_int, [_P, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]),
     "transec_transmission": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P]),
     "transec_column_contributions": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, _P, _P, _P, C.c_int]),
+    "transec_batch_column_contributions": (
+        C.c_int, [C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int]),
     "transec_apply": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _P, _P, C.c_int]),
     "transec_apply_noalloc": (C.c_int, [_P, C.c_double, C.c_int, C.c_int, C.c_int, _P, _P]),
     "transec_trace": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int]),
@@ -224,6 +229,13 @@ def transec_n_rhs(ctx) -> int:
     return int(n.value)
 
 
+def transec_autotune(ctx, energy, ik) -> dict:
+    v = [C.c_int(), C.c_int(), C.c_int()]
+    _check(ctx, load().transec_autotune(ctx, float(energy), int(ik), *[C.byref(x) for x in v]),
+           "transec_autotune")
+    return {"tile_y": v[0].value, "slab": v[1].value, "slots": v[2].value}
+
+
 def transec_transmission(ctx, energies, T_out, T_avg_out=None, status_out=None, iters_out=None):
     e = _Arr(energies, np.float64)
     t = _Arr(T_out, np.float64, writable=True)
@@ -255,6 +267,27 @@ def transec_column_contributions(ctx, energies, ik, cols, t_out, t_minus_out=Non
         so.ptr if so else None, side,
     )
     return _check(ctx, st, "transec_column_contributions", allow=(ENOCONV, EBREAKDOWN))
+
+
+def transec_batch_column_contributions(ctxs, ictx, energies, ik, cols, t_out, t_minus_out=None,
+                                       iters_out=None, status_out=None):
+    """Columns of several contexts in one solve; ``ictx`` picks each item's context."""
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    i = _Arr(ictx, np.int32)
+    e = _Arr(energies, np.float64)
+    k = _Arr(ik, np.int32)
+    c = _Arr(cols, np.int64)
+    t = _Arr(t_out, np.float64, writable=True)
+    tm = _Arr(t_minus_out, np.float64, writable=True) if t_minus_out is not None else None
+    io = _Arr(iters_out, np.int32, writable=True) if iters_out is not None else None
+    so = _Arr(status_out, np.int32, writable=True) if status_out is not None else None
+    side = _side([i, e, k, c, t, tm, io, so])
+    n = int(e.keep.numel() if hasattr(e.keep, "numel") else np.asarray(e.keep).size)
+    st = load().transec_batch_column_contributions(
+        len(ctxs), C.cast(arr, C.c_void_p), n, i.ptr, e.ptr, k.ptr, c.ptr, t.ptr,
+        tm.ptr if tm else None, io.ptr if io else None, so.ptr if so else None, side,
+    )
+    return _check(ctxs[0], st, "transec_batch_column_contributions", allow=(ENOCONV, EBREAKDOWN))
 
 
 def transec_apply(ctx, energy, ik, x, y, conj_k=False):

@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "engine.cuh"
@@ -218,13 +219,13 @@ namespace {
 
 // Columns in flight: enough point-halves per iteration to fill the GPU, bounded by
 // memory (at most half of what is free) and by the number of items.
-int choose_slots(transec_ctx* ctx, int H, size_t bytes_per_slot, long long nitems, int requested) {
+int choose_slots(long long n_mean, int H, size_t bytes_per_slot, long long nitems, int requested) {
   long long s;
   if (requested > 0) {
     s = requested;
   } else {
     const long long target = 24LL << 20;  // point-halves per iteration
-    s = (target + ctx->g.n * H - 1) / (ctx->g.n * H);
+    s = (target + n_mean * H - 1) / (n_mean * H);
     s = std::max(1LL, std::min(s, 4096LL));
   }
   size_t fr = 0, tot = 0;
@@ -241,15 +242,11 @@ template <> [[maybe_unused]] Engine<double>& engine_of<double>(transec_ctx* ctx)
 template <> [[maybe_unused]] Engine<float>& engine_of<float>(transec_ctx* ctx) { return ctx->e32; }
 
 template <typename T>
-int engine_ensure(transec_ctx* ctx, Engine<T>& eng, int S, int H) {
+int engine_ensure(transec_ctx* ctx, Engine<T>& eng, int S, int H, long long n, int nblk2,
+                  int nblk3) {
   using CT = typename Cx<T>::type;
-  const long long n = ctx->g.n;
-  const TileShape ts = choose_tiles(ctx->g, H, sizeof(CT), StencilMax<T>::threads,
-                                    ctx->opts.tile_y, ctx->opts.slab);
-  const int nblk2 = ts.ntx * ts.nty * ts.nslab;
-  const int nblk3 = (int)std::max(1LL, std::min(1024LL, (n + 256 * 8 - 1) / (256 * 8)));
-  const bool same = eng.S >= S && eng.H == H && eng.n == n && eng.nblk2 == nblk2 &&
-                    eng.nblk3 == nblk3 && eng.X != nullptr;
+  const bool same = eng.S >= S && eng.H == H && eng.n >= n && eng.nblk2 >= nblk2 &&
+                    eng.nblk3 >= nblk3 && eng.X != nullptr;
   if (!same) {
     eng.release();
     const size_t vec = (size_t)S * H * n * sizeof(CT);
@@ -265,13 +262,62 @@ int engine_ensure(transec_ctx* ctx, Engine<T>& eng, int S, int H) {
     eng.S = S;
     eng.H = H;
     eng.n = n;
+    eng.nblk2 = nblk2;
+    eng.nblk3 = nblk3;
   }
-  eng.TX = ts.TX; eng.TY = ts.TY; eng.D = ts.D; eng.ntx = ts.ntx; eng.nty = ts.nty;
-  eng.nslab = ts.nslab; eng.threads = ts.threads; eng.smem = ts.smem;
-  eng.nblk2 = nblk2;
-  eng.nblk3 = nblk3;
-  CK(prepare_stencil<T>(ctx->g.R, ts.smem));
   return TRANSEC_OK;
+}
+
+// The operators of one solve and their launch shapes for H halves: the driver
+// context alone, or every member of a batch (same device and stencil order).
+struct BatchPlan {
+  std::vector<Inst> insts;
+  long long n_max = 0;
+  double n_mean = 0;
+  int R = 0;
+  // per arithmetic (0: FP64 kernel, 1: FP32 kernel): the launch covering every member
+  int grid_x[2] = {0, 0}, grid_y[2] = {0, 0}, threads[2] = {0, 0};
+  size_t smem[2] = {0, 0};
+  int nblk3 = 1;
+};
+
+BatchPlan plan_batch(const transec_ctx* driver, const std::vector<transec_ctx*>& members, int H,
+                     bool fp32_iteration) {
+  BatchPlan b;
+  b.R = driver->g.R;
+  for (const transec_ctx* m : members) {
+    Inst in{};
+    in.g = m->g;
+    in.v = m->d_v;
+    in.v32 = m->d_v32;
+    in.gam = m->d_gam;
+    in.gl = m->d_gl;
+    in.gr = m->d_gr;
+    in.phase = m->d_phase;
+    in.lplanes = m->d_lplanes;
+    in.rplanes = m->d_rplanes;
+    in.nlp = (int)m->lplanes.size();
+    in.nrp = (int)m->rplanes.size();
+    in.nk = m->nk;
+    // the iteration kernel takes the driver's tile options; the FP64 residual
+    // replacement of the mixed form uses the default shape
+    const int ty = driver->opts.tile_y, sl = driver->opts.slab;
+    in.tile[0] = choose_tiles(m->g, H, sizeof(double2), StencilMax<double>::threads,
+                              fp32_iteration ? 0 : ty, fp32_iteration ? 0 : sl);
+    in.tile[1] = choose_tiles(m->g, H, sizeof(float2), StencilMax<float>::threads,
+                              fp32_iteration ? ty : 0, fp32_iteration ? sl : 0);
+    for (int k = 0; k < 2; ++k) {
+      b.grid_x[k] = std::max(b.grid_x[k], in.tile[k].ntx * in.tile[k].nty);
+      b.grid_y[k] = std::max(b.grid_y[k], in.tile[k].nslab);
+      b.threads[k] = std::max(b.threads[k], in.tile[k].threads);
+      b.smem[k] = std::max(b.smem[k], in.tile[k].smem);
+    }
+    b.n_max = std::max(b.n_max, m->g.n);
+    b.n_mean += (double)m->g.n / members.size();
+    b.nblk3 = std::max(b.nblk3, (int)std::min(1024LL, (m->g.n + 256 * 8 - 1) / (256 * 8)));
+    b.insts.push_back(in);
+  }
+  return b;
 }
 
 int ensure_events(transec_ctx* ctx, int n) {
@@ -299,8 +345,9 @@ void accumulate_events(transec_ctx* ctx, int C) {
 }
 
 // FP64 buffers of the mixed-precision residual replacement (see mixed.cuh).
-int mixed_ensure(transec_ctx* ctx, int S, int H, long long nblk_sig, long long nblk_part) {
-  const long long elems = (long long)S * H * ctx->g.n;
+int mixed_ensure(transec_ctx* ctx, int S, int H, long long n, long long nblk_sig,
+                 long long nblk_part) {
+  const long long elems = (long long)S * H * n;
   if (ctx->mx_elems < elems) {
     cudaFree(ctx->mx_x); cudaFree(ctx->mx_q); cudaFree(ctx->mx_p);
     ctx->mx_x = ctx->mx_q = ctx->mx_p = nullptr;
@@ -338,55 +385,69 @@ int mixed_ensure(transec_ctx* ctx, int S, int H, long long nblk_sig, long long n
 // halves: plain (T = double) or mixed precision (T = float, with FP64 residual
 // replacement).  Item and result arrays are device pointers.
 template <typename T>
-int run_engine(transec_ctx* ctx, int H, bool mixed, int nitems, const double* d_e, const int* d_ik,
+int run_engine(transec_ctx* ctx, const std::vector<transec_ctx*>& members, const int* d_item_inst,
+               int H, bool mixed, int nitems, const double* d_e, const int* d_ik,
                const long long* d_col, double* d_t, double* d_tm, int* d_it, int* d_st) {
   using CT = typename Cx<T>::type;
   Engine<T>& eng = engine_of<T>(ctx);
-  const size_t per_slot = (size_t)5 * H * ctx->g.n * sizeof(CT) +
-                          (mixed ? (size_t)3 * H * ctx->g.n * sizeof(double2) : 0);
-  const int S = choose_slots(ctx, H, per_slot, nitems, ctx->opts.slots);
-  int rc = engine_ensure<T>(ctx, eng, S, H);
+  const BatchPlan bp = plan_batch(ctx, members, H, !std::is_same<T, double>::value);
+  const int ti = std::is_same<T, double>::value ? 0 : 1;  // tile set of the iteration kernel
+  const long long nmax = bp.n_max;
+  const size_t per_slot = (size_t)5 * H * nmax * sizeof(CT) +
+                          (mixed ? (size_t)3 * H * nmax * sizeof(double2) : 0);
+  const int S = choose_slots((long long)bp.n_mean, H, per_slot, nitems, ctx->opts.slots);
+  int rc = engine_ensure<T>(ctx, eng, S, H, nmax, bp.grid_x[ti] * bp.grid_y[ti], bp.nblk3);
   if (rc) return rc;
-  // the FP64 stencil of the mixed form's residual replacement
-  const TileShape t64 = choose_tiles(ctx->g, H, sizeof(double2), StencilMax<double>::threads, 0, 0);
+  CK(prepare_stencil<T>(bp.R, bp.smem[ti]));
   if (mixed) {
-    rc = mixed_ensure(ctx, S, H, (long long)t64.ntx * t64.nty * t64.nslab, eng.nblk3);
+    rc = mixed_ensure(ctx, S, H, nmax, (long long)bp.grid_x[0] * bp.grid_y[0], bp.nblk3);
     if (rc) return rc;
-    CK(prepare_stencil<double>(ctx->g.R, t64.smem));
+    CK(prepare_stencil<double>(bp.R, bp.smem[0]));
   }
-  const int Sl = eng.S;  // may exceed S when reusing larger buffers; extra slots stay idle
+  const int ninst = (int)bp.insts.size();
+  if (ctx->insts_cap < ninst) {
+    cudaFree(ctx->d_insts);
+    ctx->d_insts = nullptr;
+    ctx->insts_cap = 0;
+    CK(cudaMalloc(&ctx->d_insts, ninst * sizeof(Inst)));
+    ctx->insts_cap = ninst;
+  }
   cudaStream_t s = ctx->s;
-  const Queue q0{0, 0, nitems, 0};
+  CK(cudaMemcpyAsync(ctx->d_insts, bp.insts.data(), ninst * sizeof(Inst), cudaMemcpyHostToDevice, s));
+  const Inst* dI = ctx->d_insts;
+  const int Sl = eng.S;  // may exceed S when reusing larger buffers; extra slots stay idle
+  Queue q0{};
+  q0.nitems = nitems;
   CK(cudaMemcpyAsync(eng.queue, &q0, sizeof(Queue), cudaMemcpyHostToDevice, s));
   CK(cudaMemsetAsync(eng.slots, 0, (size_t)Sl * sizeof(Slot), s));
-  // Only the first S slots take work: mark the rest as DONE-without-item is not
-  // needed because assign fills idle slots in order and the queue runs dry.
-  const long long n = ctx->g.n;
-  const long long stride = (long long)H * n;
+  const long long n = nmax;
+  const long long stride = (long long)H * nmax;
 
   AssignArgs aa{};
   aa.slots = eng.slots; aa.S = std::min(Sl, S); aa.H = H; aa.queue = eng.queue;
   aa.item_e = d_e; aa.item_ik = d_ik; aa.item_col = d_col;
-  aa.lplanes = ctx->d_lplanes; aa.nlp = (int)ctx->lplanes.size(); aa.nk = ctx->nk; aa.nxy = ctx->g.nxy;
+  aa.item_inst = d_item_inst; aa.insts = dI; aa.ninst = ninst;
 
   InitArgs<T> ia{};
-  ia.x = eng.X; ia.r = eng.R; ia.p = eng.P0; ia.slots = eng.slots; ia.n = n; ia.slot_stride = stride; ia.H = H;
-  const dim3 ig((unsigned)eng.nblk3, (unsigned)aa.S);
+  ia.x = eng.X; ia.r = eng.R; ia.p = eng.P0; ia.slots = eng.slots; ia.n = n; ia.slot_stride = stride;
+  ia.H = H; ia.insts = dI;
+  const dim3 ig((unsigned)bp.nblk3, (unsigned)aa.S);
 
   StencilArgs<T> sa{};
-  sa.r = eng.R; sa.q = eng.Q; sa.part = eng.sig_part; sa.slots = eng.slots; sa.phase = ctx->d_phase;
-  sa.v = sizeof(T) == 8 ? reinterpret_cast<const T*>(ctx->d_v) : reinterpret_cast<const T*>(ctx->d_v32);
-  sa.gam = ctx->d_gam; sa.g = ctx->g; sa.H = H; sa.TX = eng.TX; sa.TY = eng.TY; sa.D = eng.D;
-  sa.ntx = eng.ntx; sa.conj = 0; sa.slot_stride = stride;
-  const dim3 sg((unsigned)(eng.ntx * eng.nty), (unsigned)eng.nslab, (unsigned)aa.S);
+  sa.r = eng.R; sa.q = eng.Q; sa.part = eng.sig_part; sa.slots = eng.slots; sa.H = H; sa.conj = 0;
+  sa.slot_stride = stride; sa.insts = dI; sa.tile_idx = ti;
+  const dim3 sg((unsigned)bp.grid_x[ti], (unsigned)bp.grid_y[ti], (unsigned)aa.S);
+  const int sthreads = bp.threads[ti];
+  const size_t ssmem = bp.smem[ti];
 
   UpdateArgs<T> ua{};
-  ua.x = eng.X; ua.r = eng.R; ua.q = eng.Q; ua.sig_part = eng.sig_part; ua.sig_nblk = eng.nblk2;
-  ua.rho_part = eng.rho_part; ua.slots = eng.slots; ua.n = n; ua.slot_stride = stride; ua.H = H;
-  const dim3 ug((unsigned)eng.nblk3, (unsigned)aa.S);
+  ua.x = eng.X; ua.r = eng.R; ua.q = eng.Q; ua.sig_part = eng.sig_part;
+  ua.sig_nblk = bp.grid_x[ti] * bp.grid_y[ti]; ua.rho_part = eng.rho_part; ua.slots = eng.slots;
+  ua.n = n; ua.slot_stride = stride; ua.H = H; ua.insts = dI;
+  const dim3 ug((unsigned)bp.nblk3, (unsigned)aa.S);
 
   ScalarArgs ca{};
-  ca.rho_part = eng.rho_part; ca.nblk = eng.nblk3; ca.slots = eng.slots; ca.S = aa.S; ca.H = H;
+  ca.rho_part = eng.rho_part; ca.nblk = bp.nblk3; ca.slots = eng.slots; ca.S = aa.S; ca.H = H;
   ca.maxit = mixed ? std::min(ctx->opts.maxit, ctx->opts.mixed_maxit) : ctx->opts.maxit;
   ca.tol = ctx->opts.tol;
   // the FP32 cycle restarts only on progress (no stall rule: BiCG residuals wander for
@@ -398,23 +459,21 @@ int run_engine(transec_ctx* ctx, int H, bool mixed, int nitems, const double* d_
   // the trace reads the FP64 solution: the engine's x (plain) or x64 (mixed)
   TraceArgs<double> ta{};
   ta.x = mixed ? ctx->mx_x : reinterpret_cast<const double2*>(eng.X);
-  ta.slots = eng.slots; ta.queue = eng.queue; ta.rplanes = ctx->d_rplanes;
-  ta.nrp = (int)ctx->rplanes.size(); ta.gl = ctx->d_gl; ta.gr = ctx->d_gr; ta.res_t = d_t;
-  ta.res_tm = d_tm; ta.res_it = d_it; ta.res_status = d_st; ta.nxy = ctx->g.nxy; ta.n = n;
-  ta.slot_stride = stride; ta.H = H;
+  ta.slots = eng.slots; ta.queue = eng.queue; ta.res_t = d_t; ta.res_tm = d_tm; ta.res_it = d_it;
+  ta.res_status = d_st; ta.slot_stride = stride; ta.H = H; ta.insts = dI;
 
   // mixed precision: residual replacement stage
   MxPrepArgs mp{eng.slots, ctx->mx_slots, aa.S};
-  MxAccumArgs mac{ctx->mx_x, reinterpret_cast<float2*>(eng.X), ctx->mx_slots, n, stride, H};
+  MxAccumArgs mac{ctx->mx_x, reinterpret_cast<float2*>(eng.X), ctx->mx_slots, n, stride, H, dI};
   StencilArgs<double> s64{};
   s64.r = ctx->mx_x; s64.p_in = ctx->mx_x; s64.p_out = ctx->mx_p; s64.q = ctx->mx_q;
-  s64.part = ctx->mx_sig; s64.slots = ctx->mx_slots; s64.phase = ctx->d_phase; s64.v = ctx->d_v;
-  s64.gam = ctx->d_gam; s64.g = ctx->g; s64.H = H; s64.TX = t64.TX; s64.TY = t64.TY; s64.D = t64.D;
-  s64.ntx = t64.ntx; s64.conj = 0; s64.slot_stride = stride;
-  const dim3 sg64((unsigned)(t64.ntx * t64.nty), (unsigned)t64.nslab, (unsigned)aa.S);
-  MxFinishArgs mf{ctx->mx_q, reinterpret_cast<float2*>(eng.R), ctx->mx_slots, ctx->mx_part, n, stride, H};
-  MxScalarArgs ms{ctx->mx_part, eng.nblk3, ctx->mx_slots, eng.slots, aa.S, H, ctx->opts.tol};
-  MxInitArgs mi{ctx->mx_x, eng.slots, n, stride, H};
+  s64.part = ctx->mx_sig; s64.slots = ctx->mx_slots; s64.H = H; s64.conj = 0;
+  s64.slot_stride = stride; s64.insts = dI; s64.tile_idx = 0;
+  const dim3 sg64((unsigned)bp.grid_x[0], (unsigned)bp.grid_y[0], (unsigned)aa.S);
+  MxFinishArgs mf{ctx->mx_q, reinterpret_cast<float2*>(eng.R), ctx->mx_slots, ctx->mx_part, n,
+                  stride, H, dI};
+  MxScalarArgs ms{ctx->mx_part, bp.nblk3, ctx->mx_slots, eng.slots, aa.S, H, ctx->opts.tol};
+  MxInitArgs mi{ctx->mx_x, eng.slots, n, stride, H, dI};
 
   k_assign<<<1, 1024, 0, s>>>(aa);
   k_init<T><<<ig, 256, 0, s>>>(ia);
@@ -427,14 +486,40 @@ int run_engine(transec_ctx* ctx, int H, bool mixed, int nitems, const double* d_
     rc = ensure_events(ctx, 4 * C);
     if (rc) return rc;
   }
+  // One chunk: C iterations, the mixed form's residual replacement, trace, refill.
+  // Default: the chunk is the body of a device-side WHILE loop (a conditional graph
+  // node), so a whole solve is one graph launch; with profiling (event records are not
+  // allowed in conditional bodies) or opts.host_loop the host launches chunk by chunk.
+  const bool device_loop = !prof && !ctx->opts.host_loop;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaGraphConditionalHandle loop{};
+  if (device_loop) {
+    CK(cudaGraphCreate(&graph, 0));
+    cudaError_t eh = cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (eh == cudaSuccess) eh = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (eh == cudaSuccess)
+      eh = cudaStreamBeginCaptureToGraph(s, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+    if (eh != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return fail(ctx, TRANSEC_ECUDA, std::string("device loop set-up: ") + cudaGetErrorString(eh));
+    }
+  } else {
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  }
   for (int i = 0; i < C; ++i) {
     sa.p_in = (i % 2 == 0) ? eng.P0 : eng.P1;
     sa.p_out = (i % 2 == 0) ? eng.P1 : eng.P0;
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 0], s, cudaEventRecordExternal);
-    launch_stencil<T>(ctx->g.R, sg, eng.threads, eng.smem, s, sa);
+    launch_stencil<T>(bp.R, sg, sthreads, ssmem, s, sa);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 1], s, cudaEventRecordExternal);
     ua.p = sa.p_out;
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 2], s, cudaEventRecordExternal);
@@ -445,7 +530,7 @@ int run_engine(transec_ctx* ctx, int H, bool mixed, int nitems, const double* d_
   if (mixed) {
     k_mx_prep<<<(aa.S + 255) / 256, 256, 0, s>>>(mp);
     k_mx_accum<<<ig, 256, 0, s>>>(mac);
-    launch_stencil<double>(ctx->g.R, sg64, t64.threads, t64.smem, s, s64);
+    launch_stencil<double>(bp.R, sg64, bp.threads[0], bp.smem[0], s, s64);
     k_mx_finish<<<ig, 256, 0, s>>>(mf);
     k_mx_scalars<<<cgrid, 256, 0, s>>>(ms);
   }
@@ -453,10 +538,17 @@ int run_engine(transec_ctx* ctx, int H, bool mixed, int nitems, const double* d_
   k_assign<<<1, 1024, 0, s>>>(aa);
   k_init<T><<<ig, 256, 0, s>>>(ia);
   if (mixed) k_mx_init<<<ig, 256, 0, s>>>(mi);
-  cudaMemcpyAsync(ctx->h_harvest, &eng.queue->harvested, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (device_loop) {
+    k_continue<<<1, 1, 0, s>>>(loop, eng.queue);
+  } else {
+    cudaMemcpyAsync(ctx->h_harvest, &eng.queue->harvested, sizeof(int), cudaMemcpyDeviceToHost, s);
+  }
   {
-    cudaError_t e1 = cudaStreamEndCapture(s, &graph);
+    cudaGraph_t captured = nullptr;
+    cudaError_t e1 = cudaStreamEndCapture(s, &captured);
+    if (!device_loop) graph = captured;
     if (e1 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();
       return fail(ctx, TRANSEC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
     }
@@ -469,21 +561,37 @@ int run_engine(transec_ctx* ctx, int H, bool mixed, int nitems, const double* d_
       return fail(ctx, TRANSEC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
     }
   }
-  const long long per_chunk = 3LL * C + 3 + (mixed ? 6 : 0);
+  const long long per_chunk = 3LL * C + 3 + (mixed ? 6 : 0) + (device_loop ? 1 : 0);
   const long long max_chunks =
       ((long long)nitems / std::max(1, aa.S) + 2) * ((long long)ctx->opts.maxit / C + 2) + 16;
+  // chunks per device-loop launch: a launch always ends, and the host re-checks
+  const int per_launch = 4096;
   long long chunks = 0;
   int rcode = TRANSEC_OK;
   *ctx->h_harvest = 0;
   while (true) {
-    cudaError_t e3 = cudaGraphLaunch(exec, s);
-    if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(s);
+    cudaError_t e3 = cudaSuccess;
+    if (device_loop) {
+      const int lim = (int)std::min<long long>(chunks + per_launch, 1LL << 30);
+      e3 = cudaMemcpyAsync(&eng.queue->limit, &lim, sizeof(int), cudaMemcpyHostToDevice, s);
+      if (e3 == cudaSuccess) e3 = cudaGraphLaunch(exec, s);
+      Queue qh{};
+      if (e3 == cudaSuccess) e3 = cudaMemcpyAsync(&qh, eng.queue, sizeof(Queue), cudaMemcpyDeviceToHost, s);
+      if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(s);
+      if (e3 == cudaSuccess) {
+        chunks = qh.chunks;
+        *ctx->h_harvest = qh.harvested;
+      }
+    } else {
+      e3 = cudaGraphLaunch(exec, s);
+      if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(s);
+      if (e3 == cudaSuccess) ++chunks;
+    }
     if (e3 != cudaSuccess) {
       cudaGetLastError();
       rcode = fail(ctx, TRANSEC_ECUDA, std::string("solver chunk: ") + cudaGetErrorString(e3));
       break;
     }
-    ++chunks;
     if (prof) accumulate_events(ctx, C);
     if (*ctx->h_harvest >= nitems) break;
     if (chunks > max_chunks) {
@@ -493,12 +601,17 @@ int run_engine(transec_ctx* ctx, int H, bool mixed, int nitems, const double* d_
   }
   ctx->launches += (mixed ? 3 : 2) + chunks * per_chunk;
   if (rcode == TRANSEC_OK && d_it) {
-    std::vector<int> its(nitems);
-    if (cudaMemcpy(its.data(), d_it, nitems * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess) {
-      long long tot = 0;
-      for (int v : its) tot += v;
-      ctx->point_applies += tot * H * ctx->g.n;
+    std::vector<int> its(nitems), inst(nitems, 0);
+    bool ok = cudaMemcpy(its.data(), d_it, nitems * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok && d_item_inst)
+      ok = cudaMemcpy(inst.data(), d_item_inst, nitems * sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (ok) {
+      for (int i = 0; i < nitems; ++i) {
+        const int ii = (inst[i] >= 0 && inst[i] < ninst) ? inst[i] : 0;
+        ctx->point_applies += (long long)its[i] * H * bp.insts[ii].g.n;
+      }
     }
+    cudaGetLastError();
   }
   cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
@@ -533,12 +646,17 @@ int check_ready(transec_ctx* ctx) {
 }
 
 // Items with device-resident arrays -> results in device arrays, for one method group.
-int solve_items(transec_ctx* ctx, int H, int nitems, const double* d_e, const int* d_ik,
-                const long long* d_col, double* d_t, double* d_tm, int* d_it, int* d_st) {
+// Items of a batch (members[item_inst[i]], or ctx alone when item_inst is NULL), solved
+// in one engine run with the driver context's options, buffers and stream.
+int solve_batch(transec_ctx* ctx, const std::vector<transec_ctx*>& members, const int* d_inst,
+                int H, int nitems, const double* d_e, const int* d_ik, const long long* d_col,
+                double* d_t, double* d_tm, int* d_it, int* d_st) {
   if (nitems == 0) return TRANSEC_OK;
   if (ctx->opts.precision != TRANSEC_PREC_MIXED)
-    return run_engine<double>(ctx, H, false, nitems, d_e, d_ik, d_col, d_t, d_tm, d_it, d_st);
-  int rc = run_engine<float>(ctx, H, true, nitems, d_e, d_ik, d_col, d_t, d_tm, d_it, d_st);
+    return run_engine<double>(ctx, members, d_inst, H, false, nitems, d_e, d_ik, d_col, d_t, d_tm,
+                              d_it, d_st);
+  int rc = run_engine<float>(ctx, members, d_inst, H, true, nitems, d_e, d_ik, d_col, d_t, d_tm,
+                             d_it, d_st);
   if (rc != TRANSEC_OK) return rc;
   // Columns the mixed form could not finish (not converged, or a breakdown of the
   // FP32 recurrence) are solved again with the plain FP64 engine.
@@ -551,22 +669,27 @@ int solve_items(transec_ctx* ctx, int H, int nitems, const double* d_e, const in
   if (redo.empty()) return TRANSEC_OK;
   const int m = (int)redo.size();
   std::vector<double> he(nitems);
-  std::vector<int> hk(nitems), hit(nitems);
+  std::vector<int> hk(nitems), hit(nitems), hi(nitems, 0);
   std::vector<long long> hc(nitems);
+  if (d_inst)
+    CK(cudaMemcpyAsync(hi.data(), d_inst, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaMemcpyAsync(he.data(), d_e, nitems * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaMemcpyAsync(hk.data(), d_ik, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaMemcpyAsync(hc.data(), d_col, nitems * sizeof(long long), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaMemcpyAsync(hit.data(), d_it, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaStreamSynchronize(ctx->s));
   std::vector<double> re(m);
-  std::vector<int> rk(m);
+  std::vector<int> rk(m), ri(m);
   std::vector<long long> rcl(m);
   for (int u = 0; u < m; ++u) {
     re[u] = he[redo[u]];
     rk[u] = hk[redo[u]];
     rcl[u] = hc[redo[u]];
+    ri[u] = hi[redo[u]];
   }
-  DevBuf be, bk, bc, bt, btm, bit, bst;
+  DevBuf be, bk, bc, bt, btm, bit, bst, bi;
+  CK(cudaMalloc(&bi.p, m * sizeof(int)));
+  CK(cudaMemcpyAsync(bi.p, ri.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
   CK(cudaMalloc(&be.p, m * sizeof(double)));
   CK(cudaMalloc(&bk.p, m * sizeof(int)));
   CK(cudaMalloc(&bc.p, m * sizeof(long long)));
@@ -577,8 +700,9 @@ int solve_items(transec_ctx* ctx, int H, int nitems, const double* d_e, const in
   CK(cudaMemcpyAsync(be.p, re.data(), m * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
   CK(cudaMemcpyAsync(bk.p, rk.data(), m * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
   CK(cudaMemcpyAsync(bc.p, rcl.data(), m * sizeof(long long), cudaMemcpyHostToDevice, ctx->s));
-  rc = run_engine<double>(ctx, H, false, m, (double*)be.p, (int*)bk.p, (long long*)bc.p,
-                          (double*)bt.p, (double*)btm.p, (int*)bit.p, (int*)bst.p);
+  rc = run_engine<double>(ctx, members, d_inst ? (const int*)bi.p : nullptr, H, false, m,
+                          (double*)be.p, (int*)bk.p, (long long*)bc.p, (double*)bt.p,
+                          (double*)btm.p, (int*)bit.p, (int*)bst.p);
   if (rc != TRANSEC_OK) return rc;
   std::vector<double> t(m), tm(m);
   std::vector<int> it(m), s2(m);
@@ -600,8 +724,15 @@ int solve_items(transec_ctx* ctx, int H, int nitems, const double* d_e, const in
   return TRANSEC_OK;
 }
 
-// Host item lists -> host results (one method group).
-int solve_host_items(transec_ctx* ctx, int H, const std::vector<double>& e,
+int solve_items(transec_ctx* ctx, int H, int nitems, const double* d_e, const int* d_ik,
+                const long long* d_col, double* d_t, double* d_tm, int* d_it, int* d_st) {
+  return solve_batch(ctx, {ctx}, nullptr, H, nitems, d_e, d_ik, d_col, d_t, d_tm, d_it, d_st);
+}
+
+// Host item lists -> host results (one method group); `inst` (may be empty) holds the
+// batch member of each item.
+int solve_host_items(transec_ctx* ctx, const std::vector<transec_ctx*>& members,
+                     const std::vector<int>& inst, int H, const std::vector<double>& e,
                      const std::vector<int>& ik, const std::vector<long long>& col,
                      std::vector<double>& t, std::vector<double>& tm, std::vector<int>& it,
                      std::vector<int>& st) {
@@ -622,8 +753,13 @@ int solve_host_items(transec_ctx* ctx, int H, const std::vector<double>& e,
   CK(cudaMemcpyAsync(be.p, e.data(), nitems * sizeof(double), cudaMemcpyHostToDevice, ctx->s));
   CK(cudaMemcpyAsync(bk.p, ik.data(), nitems * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
   CK(cudaMemcpyAsync(bc.p, col.data(), nitems * sizeof(long long), cudaMemcpyHostToDevice, ctx->s));
-  int rc = solve_items(ctx, H, nitems, (double*)be.p, (int*)bk.p, (long long*)bc.p, (double*)bt.p,
-                       (double*)btm.p, (int*)bit.p, (int*)bst.p);
+  DevBuf bi;
+  if (!inst.empty()) {
+    CK(cudaMalloc(&bi.p, nitems * sizeof(int)));
+    CK(cudaMemcpyAsync(bi.p, inst.data(), nitems * sizeof(int), cudaMemcpyHostToDevice, ctx->s));
+  }
+  int rc = solve_batch(ctx, members, (const int*)bi.p, H, nitems, (double*)be.p, (int*)bk.p,
+                       (long long*)bc.p, (double*)bt.p, (double*)btm.p, (int*)bit.p, (int*)bst.p);
   if (rc != TRANSEC_OK && rc != TRANSEC_ENOCONV && rc != TRANSEC_EBREAKDOWN) return rc;
   CK(cudaMemcpyAsync(t.data(), bt.p, nitems * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   CK(cudaMemcpyAsync(tm.data(), btm.p, nitems * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
@@ -901,7 +1037,7 @@ int transec_column_contributions(transec_ctx* ctx, int nitems, const double* ene
     std::vector<long long> c(cols, cols + nitems);
     std::vector<double> t, tm;
     std::vector<int> it, st;
-    rc = solve_host_items(ctx, H, e, hik, c, t, tm, it, st);
+    rc = solve_host_items(ctx, {ctx}, {}, H, e, hik, c, t, tm, it, st);
     if (rc != TRANSEC_OK && rc != TRANSEC_ENOCONV && rc != TRANSEC_EBREAKDOWN) return rc;
     std::memcpy(t_out, t.data(), nitems * sizeof(double));
     if (t_minus_out) std::memcpy(t_minus_out, tm.data(), nitems * sizeof(double));
@@ -914,6 +1050,152 @@ int transec_column_contributions(transec_ctx* ctx, int nitems, const double* ene
   if (rc) return rc;
   if (worst != TRANSEC_OK) ctx->err = std::string("some columns failed: ") + transec_status_string(worst);
   return worst;
+}
+
+int transec_batch_column_contributions(int nctx, transec_ctx* const* ctxs, int nitems,
+                                       const int* ictx, const double* energies, const int* ik,
+                                       const int64_t* cols, double* t_out, double* t_minus_out,
+                                       int* iters_out, int* status_out, int on_device) {
+  if (nctx < 1 || !ctxs || !ctxs[0]) return TRANSEC_EINVAL;
+  transec_ctx* ctx = ctxs[0];
+  std::vector<transec_ctx*> members(ctxs, ctxs + nctx);
+  for (transec_ctx* m : members) {
+    if (!m) return fail(ctx, TRANSEC_EINVAL, "NULL context in batch");
+    int rc = check_ready(m);
+    if (rc) return fail(ctx, rc, std::string("batch member not ready: ") + m->err);
+    if (m->device != ctx->device) return fail(ctx, TRANSEC_EINVAL, "batch contexts on different devices");
+    if (m->g.R != ctx->g.R) return fail(ctx, TRANSEC_EINVAL, "batch contexts with different stencil orders");
+  }
+  if (nitems < 0) return fail(ctx, TRANSEC_EINVAL, "nitems < 0");
+  if (nitems == 0) return TRANSEC_OK;
+  if (!ictx || !energies || !ik || !cols || !t_out) return fail(ctx, TRANSEC_EINVAL, "NULL item or output array");
+  DeviceGuard dg(ctx->device);
+  int rc = begin_call(ctx);
+  if (rc) return rc;
+  std::vector<int> hik(nitems), hic(nitems);
+  if (on_device) {
+    CK(cudaMemcpyAsync(hik.data(), ik, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaMemcpyAsync(hic.data(), ictx, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+  } else {
+    hik.assign(ik, ik + nitems);
+    hic.assign(ictx, ictx + nitems);
+  }
+  int H = 0;
+  for (int i = 0; i < nitems; ++i) {
+    if (hic[i] < 0 || hic[i] >= nctx) return fail(ctx, TRANSEC_EINVAL, "context index out of range");
+    const transec_ctx* m = members[hic[i]];
+    if (hik[i] < 0 || hik[i] >= m->nk) return fail(ctx, TRANSEC_EINVAL, "k index out of range");
+    const bool rp = real_phase(m->kfrac[2 * hik[i]], m->kfrac[2 * hik[i] + 1]);
+    const int h = ctx->opts.method == TRANSEC_METHOD_BICG ? 2 : (rp ? 1 : 2);
+    if (ctx->opts.method == TRANSEC_METHOD_COCG && !rp)
+      return fail(ctx, TRANSEC_EINVAL, "COCG requested for a k-point with complex Bloch phase");
+    H = std::max(H, h);
+  }
+  int worst = TRANSEC_OK;
+  if (on_device) {
+    DevBuf btm, bit, bst;
+    double* dtm = t_minus_out;
+    int* dit = iters_out;
+    int* dst = status_out;
+    if (!dtm) { CK(cudaMalloc(&btm.p, nitems * sizeof(double))); dtm = (double*)btm.p; }
+    if (!dit) { CK(cudaMalloc(&bit.p, nitems * sizeof(int))); dit = (int*)bit.p; }
+    if (!dst) { CK(cudaMalloc(&bst.p, nitems * sizeof(int))); dst = (int*)bst.p; }
+    rc = solve_batch(ctx, members, ictx, H, nitems, energies, ik, (const long long*)cols, t_out,
+                     dtm, dit, dst);
+    if (rc != TRANSEC_OK) return rc;
+    std::vector<int> hs(nitems);
+    CK(cudaMemcpyAsync(hs.data(), dst, nitems * sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+    CK(cudaStreamSynchronize(ctx->s));
+    for (int v : hs)
+      if (severity(v) > severity(worst)) worst = v;
+  } else {
+    std::vector<double> e(energies, energies + nitems);
+    std::vector<long long> c(cols, cols + nitems);
+    std::vector<double> t, tm;
+    std::vector<int> it, st;
+    rc = solve_host_items(ctx, members, hic, H, e, hik, c, t, tm, it, st);
+    if (rc != TRANSEC_OK && rc != TRANSEC_ENOCONV && rc != TRANSEC_EBREAKDOWN) return rc;
+    std::memcpy(t_out, t.data(), nitems * sizeof(double));
+    if (t_minus_out) std::memcpy(t_minus_out, tm.data(), nitems * sizeof(double));
+    if (iters_out) std::memcpy(iters_out, it.data(), nitems * sizeof(int));
+    if (status_out) std::memcpy(status_out, st.data(), nitems * sizeof(int));
+    for (int v : st)
+      if (severity(v) > severity(worst)) worst = v;
+  }
+  rc = end_call(ctx);
+  if (rc) return rc;
+  if (worst != TRANSEC_OK) ctx->err = std::string("some columns failed: ") + transec_status_string(worst);
+  return worst;
+}
+
+int transec_autotune(transec_ctx* ctx, double energy, int ik, int* tile_y_out, int* slab_out,
+                     int* slots_out) {
+  int rc = check_ready(ctx);
+  if (rc) return rc;
+  if (ik < 0 || ik >= ctx->nk || !std::isfinite(energy)) return fail(ctx, TRANSEC_EINVAL, "bad autotune arguments");
+  DeviceGuard dg(ctx->device);
+  const transec_solver_opts saved = ctx->opts;
+  const int H = halves_for(ctx, ik);
+  if (H < 0) return fail(ctx, TRANSEC_EINVAL, "COCG requested for a k-point with complex Bloch phase");
+  const bool fp64 = saved.precision == TRANSEC_PREC_FP64;
+  const int maxthreads = fp64 ? StencilMax<double>::threads : StencilMax<float>::threads;
+  const int tx = std::min(ctx->g.nx, 32);
+  const int ylim = std::max(1, std::min(ctx->g.ny, maxthreads / (tx * H)));
+  std::vector<int> tys = {0};
+  for (int v : {ylim, ylim / 2, 8, 4})
+    if (v >= 1 && v <= ylim && std::find(tys.begin(), tys.end(), v) == tys.end()) tys.push_back(v);
+  std::vector<int> slabs = {16, 32, 64, 128};
+  const long long target = 24LL << 20;
+  const int s0 = (int)std::max(1LL, std::min(4096LL, (target + ctx->g.n * H - 1) / (ctx->g.n * H)));
+  std::vector<int> slots = {std::max(1, s0 / 2), s0, std::min(4096, 2 * s0)};
+  const long long nrhs = (long long)ctx->lplanes.size() * ctx->g.nxy;
+  double best = -1.0;
+  int by = 0, bs = 0, bS = s0;
+  for (int ty : tys)
+    for (int sl : slabs)
+      for (int S : slots) {
+        ctx->opts = saved;
+        ctx->opts.tile_y = ty;
+        ctx->opts.slab = sl;
+        ctx->opts.slots = S;
+        ctx->opts.maxit = 32;
+        ctx->opts.mixed_maxit = 32;
+        ctx->opts.profile = 1;
+        ctx->opts.host_loop = 1;
+        std::vector<double> e(S, energy);
+        std::vector<int> k(S, ik);
+        std::vector<long long> c(S);
+        for (int u = 0; u < S; ++u) c[u] = (long long)u % std::max(1LL, nrhs);
+        std::vector<double> t, tm;
+        std::vector<int> it, st;
+        transec_stats_reset(ctx);
+        rc = begin_call(ctx);
+        if (rc == TRANSEC_OK) rc = solve_host_items(ctx, {ctx}, {}, H, e, k, c, t, tm, it, st);
+        if (rc == TRANSEC_OK || rc == TRANSEC_ENOCONV || rc == TRANSEC_EBREAKDOWN) rc = end_call(ctx);
+        if (rc != TRANSEC_OK) {
+          ctx->opts = saved;
+          return rc;
+        }
+        const double ms = ctx->stencil_ms + ctx->update_ms;
+        // the fallback re-solve of the mixed form is not part of the candidate's rate
+        const double rate = ms > 0 ? (double)ctx->point_applies / ms : 0.0;
+        if (rate > best) {
+          best = rate;
+          by = ty;
+          bs = sl;
+          bS = S;
+        }
+      }
+  ctx->opts = saved;
+  ctx->opts.tile_y = by;
+  ctx->opts.slab = bs;
+  ctx->opts.slots = bS;
+  transec_stats_reset(ctx);
+  if (tile_y_out) *tile_y_out = by;
+  if (slab_out) *slab_out = bs;
+  if (slots_out) *slots_out = bS;
+  return TRANSEC_OK;
 }
 
 int transec_transmission(transec_ctx* ctx, int ne, const double* energies, double* T_out,
@@ -967,7 +1249,7 @@ int transec_transmission(transec_ctx* ctx, int ne, const double* energies, doubl
         }
       std::vector<double> t, tm;
       std::vector<int> it, st;
-      rc = solve_host_items(ctx, hgrp, ie, ik, ic, t, tm, it, st);
+      rc = solve_host_items(ctx, {ctx}, {}, hgrp, ie, ik, ic, t, tm, it, st);
       if (rc != TRANSEC_OK && rc != TRANSEC_ENOCONV && rc != TRANSEC_EBREAKDOWN) return rc;
       size_t u = 0;
       for (size_t pi = b0; pi < b1; ++pi) {
@@ -1133,6 +1415,7 @@ void transec_destroy(transec_ctx* ctx) {
   ctx->e32.release();
   cudaFree(ctx->mx_x); cudaFree(ctx->mx_q); cudaFree(ctx->mx_p);
   cudaFree(ctx->mx_sig); cudaFree(ctx->mx_part); cudaFree(ctx->mx_slots);
+  cudaFree(ctx->d_insts);
   cudaFree(ctx->d_v); cudaFree(ctx->d_v32);
   cudaFree(ctx->d_gl); cudaFree(ctx->d_gr); cudaFree(ctx->d_gam);
   cudaFree(ctx->d_lplanes); cudaFree(ctx->d_rplanes); cudaFree(ctx->d_phase);

@@ -31,6 +31,29 @@ struct Geometry {
   double diag_c;  // c_0/2 * (1/hx^2 + 1/hy^2 + 1/hz^2)
 };
 
+// Launch shape of the stencil for one geometry.
+struct TileShape {
+  int TX, TY, D, ntx, nty, nslab, threads;
+  size_t smem;
+};
+
+// One operator of a solve: geometry, its device arrays and the stencil's launch
+// shapes (tile[0] for the FP64 kernel, tile[1] for the FP32 one).  A batch of
+// operators of different sizes shares one slot engine through a table of these.
+struct Inst {
+  Geometry g;
+  const double* v;
+  const float* v32;
+  const double* gam;     // Gamma_L + Gamma_R per plane
+  const double* gl;      // Gamma_L per plane
+  const double* gr;      // Gamma_R per plane
+  const double2* phase;  // [nk][2][2][kPhaseN]
+  const int* lplanes;    // planes with Gamma_L > 0
+  const int* rplanes;    // planes with Gamma_R > 0
+  int nlp, nrp, nk, pad;
+  TileShape tile[2];
+};
+
 // Per-slot solver state (device resident).
 struct Slot {
   int status;     // SlotStatus
@@ -39,6 +62,8 @@ struct Slot {
   int result;     // per-item status code once DONE (0 = converged)
   int ik;         // k-point index
   int init;       // set by assign when the vectors must be (re)initialised
+  int inst;       // operator (index into the Inst table) of the item
+  int pad0;
   long long j;    // grid index of the right-hand side e_j
   double e;       // energy (Hartree)
   double2 rho;    // <r, r> in the pairing form
@@ -57,7 +82,9 @@ struct Queue {
   int next;       // next unassigned item
   int harvested;  // items whose result has been written
   int nitems;
-  int pad;
+  int chunks;     // chunks run so far (device-side loop)
+  int limit;      // the device-side loop stops at this chunk count
+  int pad[3];
 };
 
 // --- small complex helpers -------------------------------------------------------

@@ -36,12 +36,6 @@ struct Engine {
   void release();
 };
 
-// Launch shape of the stencil for a geometry.
-struct TileShape {
-  int TX, TY, D, ntx, nty, nslab, threads;
-  size_t smem;
-};
-
 TileShape choose_tiles(const Geometry& g, int H, int elem_bytes, int max_threads, int tile_y,
                        int slab);
 
@@ -93,6 +87,9 @@ struct transec_ctx {
   long long mx_sig_elems = 0;
   long long mx_part_elems = 0;
   int mx_S = 0;
+  // operator table of the last solve (one entry, or one per member of a batch)
+  transec::Inst* d_insts = nullptr;
+  int insts_cap = 0;
   // pinned host word for the harvested counter
   int* h_harvest = nullptr;
   // counters since the last transec_stats_reset

@@ -116,8 +116,17 @@ struct StencilArgs {
   Geometry g;
   int H, TX, TY, D, ntx;
   int conj;             // 1: swap the phase tables (apply A^T to half 0)
-  long long slot_stride;  // H * n
+  long long slot_stride;  // H * n (the largest n of a batch)
+  // batch mode: when insts is set, each slot's operator, arrays and launch shape
+  // come from insts[slot.inst] (tile[tile_idx]) instead of the fields above; blocks
+  // past that operator's tiles or slabs only write zero partial sums
+  const Inst* insts;
+  int tile_idx;
 };
+
+template <typename T> __device__ inline const T* inst_potential(const Inst& in);
+template <> __device__ inline const double* inst_potential<double>(const Inst& in) { return in.v; }
+template <> __device__ inline const float* inst_potential<float>(const Inst& in) { return in.v32; }
 
 // Block = TX*TY*H threads (rounded up to whole warps), one grid point (x, y) per thread and half, marching over
 // the z-slab [z0, z0 + D) with a register queue of the 2R+1 planes around the
@@ -141,41 +150,66 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
   const double e = stp->e;
   const int ik = stp->ik;
 
-  const int nx = a.g.nx, ny = a.g.ny, nz = a.g.nz;
-  const long long nxy = a.g.nxy;
-  const int npt = a.TX * a.TY;
+  // operator and launch shape: kernel arguments, or the slot's batch entry
+  const Geometry* gp = &a.g;
+  const T* vp = a.v;
+  const double* gamp = a.gam;
+  const double2* phase = a.phase;
+  int TX = a.TX, TY = a.TY, D = a.D, ntx = a.ntx;
+  bool beyond = false;
+  if (a.insts) {
+    const Inst& in = a.insts[stp->inst];
+    gp = &in.g;
+    vp = inst_potential<T>(in);
+    gamp = in.gam;
+    phase = in.phase;
+    const TileShape& ts = in.tile[a.tile_idx];
+    TX = ts.TX; TY = ts.TY; D = ts.D; ntx = ts.ntx;
+    beyond = (int)blockIdx.x >= ts.ntx * ts.nty || (int)blockIdx.y >= ts.nslab;
+  }
+  if (beyond) {
+    if (threadIdx.x == 0) {
+      double* o = a.part + ((size_t)slot * gridDim.x * gridDim.y + blockIdx.x + gridDim.x * blockIdx.y) * 2;
+      o[0] = 0.0;
+      o[1] = 0.0;
+    }
+    return;
+  }
+  const int nx = gp->nx, ny = gp->ny, nz = gp->nz;
+  const long long nxy = gp->nxy;
+  const int npt = TX * TY;
   const int t = threadIdx.x;
-  // the block is rounded up to whole warps; threads past TX*TY*H only join the
-  // barriers and the reductions
+  // the block is rounded up to whole warps (and, in a batch, to the largest tile);
+  // threads past TX*TY*H only join the barriers and the reductions
   const bool worker = t < npt * a.H;
   const int half = worker ? t / npt : 0;
   const int lt = worker ? t - half * npt : 0;
-  const int tx = lt % a.TX, ty = lt / a.TX;
-  const int x0 = (blockIdx.x % a.ntx) * a.TX, y0 = (blockIdx.x / a.ntx) * a.TY;
+  const int tx = lt % TX, ty = lt / TX;
+  const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
   const int gx = x0 + tx, gy = y0 + ty;
   const bool inside = worker && (gx < nx) && (gy < ny);
-  const int z0 = blockIdx.y * a.D;
-  const int z1 = min(z0 + a.D, nz);
-  const int SW = a.TX + 2 * R;
-  const int SHt = a.TY + 2 * R;
+  const int z0 = blockIdx.y * D;
+  const int z1 = min(z0 + D, nz);
+  const int SW = TX + 2 * R;
+  const int SHt = TY + 2 * R;
   CT* my = sm + half * SW * SHt;
-  const long long base = (long long)slot * a.slot_stride + (long long)half * a.g.n;
+  const long long base = (long long)slot * a.slot_stride + (long long)half * gp->n;
   const CT* __restrict__ r = a.r + base;
   const CT* __restrict__ pin = a.p_in + base;
   CT* __restrict__ pout = a.p_out + base;
   CT* __restrict__ q = a.q + base;
   const CT beta = cfrom<CT>(beta_d);
-  const double2* ph = a.phase + (size_t)(ik * 2 + (half ^ a.conj)) * 2 * kPhaseN;
+  const double2* ph = phase + (size_t)(ik * 2 + (half ^ a.conj)) * 2 * kPhaseN;
   const long long pidx = (long long)gx + (long long)nx * gy;
 
   T kx[R + 1], ky[R + 1], kz[R + 1];
 #pragma unroll
   for (int m = 1; m <= R; ++m) {
-    kx[m] = (T)a.g.kx[m];
-    ky[m] = (T)a.g.ky[m];
-    kz[m] = (T)a.g.kz[m];
+    kx[m] = (T)gp->kx[m];
+    ky[m] = (T)gp->ky[m];
+    kz[m] = (T)gp->kz[m];
   }
-  const T ediag = (T)(e + a.g.diag_c);
+  const T ediag = (T)(e + gp->diag_c);
 
   auto pnew = [&](long long off) -> CT {
     const CT rr = r[off], pp = pin[off];
@@ -205,7 +239,7 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
   }
 
   DotAcc<T> sg;
-  const int nh = 2 * R * (a.TX + a.TY);
+  const int nh = 2 * R * (TX + TY);
   for (int zc = z0; zc < z1; ++zc) {
 #pragma unroll
     for (int m = 0; m < 2 * R; ++m) qv[m] = qv[m + 1];
@@ -217,23 +251,23 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
     if (worker) my[(ty + R) * SW + tx + R] = inside ? c : wrapped(gx, gy, zc);
     for (int h = worker ? lt : nh; h < nh; h += npt) {
       int hx, hy;
-      if (h < 2 * R * a.TY) {
+      if (h < 2 * R * TY) {
         const int row = h / (2 * R), k = h - row * 2 * R;
         hy = row + R;
-        hx = (k < R) ? k : a.TX + k;
+        hx = (k < R) ? k : TX + k;
       } else {
-        const int h2 = h - 2 * R * a.TY;
+        const int h2 = h - 2 * R * TY;
         const int col = h2 / (2 * R), k = h2 - col * 2 * R;
         hx = col + R;
-        hy = (k < R) ? k : a.TY + k;
+        hy = (k < R) ? k : TY + k;
       }
       my[hy * SW + hx] = wrapped(x0 + hx - R, y0 + hy - R, zc);
     }
     __syncthreads();
     if (inside) {
       const long long off = (long long)zc * nxy + pidx;
-      const T dr = ediag - a.v[off];
-      const T di = (T)a.gam[zc];
+      const T dr = ediag - vp[off];
+      const T di = (T)gamp[zc];
       CT acc;
       acc.x = dr * c.x - di * c.y;
       acc.y = dr * c.y + di * c.x;
@@ -282,6 +316,7 @@ struct UpdateArgs {
   const Slot* slots;
   long long n, slot_stride;
   int H;
+  const Inst* insts;       // batch mode: the slot's grid size comes from its operator
 };
 
 template <typename T>
@@ -292,6 +327,7 @@ __global__ void __launch_bounds__(256) k_update(const UpdateArgs<T> a) {
   const int slot = blockIdx.y;
   const Slot* stp = a.slots + slot;
   if (stp->status != SLOT_ACTIVE) return;
+  const long long n = a.insts ? a.insts[stp->inst].g.n : a.n;
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     double sx = 0.0, sy = 0.0;
@@ -309,13 +345,13 @@ __global__ void __launch_bounds__(256) k_update(const UpdateArgs<T> a) {
   const long long base = (long long)slot * a.slot_stride;
   DotAcc<T> rr;
   T n0 = 0, n1 = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     CT rv[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (h >= a.H) break;
-      const long long off = base + (long long)h * a.n + i;
+      const long long off = base + (long long)h * n + i;
       const CT pp = a.p[off], qq = a.q[off];
       CT xx = a.x[off], rr = a.r[off];
       xx.x += al.x * pp.x - al.y * pp.y;
@@ -427,6 +463,7 @@ struct TraceArgs {
   int* res_status;
   long long nxy, n, slot_stride;
   int H;
+  const Inst* insts;       // batch mode: planes, profiles and sizes of the slot's operator
 };
 
 template <typename TX>
@@ -436,23 +473,32 @@ __global__ void __launch_bounds__(256) k_trace(const TraceArgs<TX> a) {
   const int slot = blockIdx.x;
   Slot* st = a.slots + slot;
   if (st->status != SLOT_DONE) return;
+  const int* rplanes = a.rplanes;
+  const double* gl = a.gl;
+  const double* gr = a.gr;
+  int nrp = a.nrp;
+  long long nxy = a.nxy, n = a.n;
+  if (a.insts) {
+    const Inst& in = a.insts[st->inst];
+    rplanes = in.rplanes; gl = in.gl; gr = in.gr; nrp = in.nrp; nxy = in.g.nxy; n = in.g.n;
+  }
   double acc[2] = {0.0, 0.0};
-  const long long tot = (long long)a.nrp * a.nxy;
+  const long long tot = (long long)nrp * nxy;
   for (int h = 0; h < a.H; ++h) {
-    const CT* x = a.x + (long long)slot * a.slot_stride + (long long)h * a.n;
+    const CT* x = a.x + (long long)slot * a.slot_stride + (long long)h * n;
     double s = 0.0;
     for (long long u = threadIdx.x; u < tot; u += blockDim.x) {
-      const int pl = a.rplanes[u / a.nxy];
-      const CT v = x[(long long)pl * a.nxy + (u % a.nxy)];
+      const int pl = rplanes[u / nxy];
+      const CT v = x[(long long)pl * nxy + (u % nxy)];
       const double vx = (double)v.x, vy = (double)v.y;
-      s += a.gr[pl] * (vx * vx + vy * vy);
+      s += gr[pl] * (vx * vx + vy * vy);
     }
     acc[h] = s;
   }
   block_sum<2>(acc, red);
   if (threadIdx.x == 0) {
     const int item = st->item;
-    const double glj = a.gl[st->j / a.nxy];
+    const double glj = gl[st->j / nxy];
     double t0 = 4.0 * glj * acc[0];
     double t1 = a.H == 2 ? 4.0 * glj * acc[1] : t0;
     if (st->result != kOK) {
@@ -483,6 +529,9 @@ struct AssignArgs {
   const int* lplanes;   // planes with Gamma_L > 0
   int nlp, nk;
   long long nxy;
+  const int* item_inst; // batch mode: operator of each item (NULL: all items use insts[0])
+  const Inst* insts;    // batch mode: when set, lplanes / nlp / nk / nxy come from here
+  int ninst;
 };
 
 static __global__ void __launch_bounds__(1024) k_assign(const AssignArgs a) {
@@ -492,7 +541,6 @@ static __global__ void __launch_bounds__(1024) k_assign(const AssignArgs a) {
   if (tid == 0) s_next = a.queue->next;
   __syncthreads();
   const int nitems = a.queue->nitems;
-  const long long nrhs = (long long)a.nlp * a.nxy;
   for (int base = 0; base < a.S; base += blockDim.x) {
     const int s = base + tid;
     int need = 0;
@@ -521,6 +569,16 @@ static __global__ void __launch_bounds__(1024) k_assign(const AssignArgs a) {
       const double e = a.item_e[item];
       const int ik = a.item_ik[item];
       const long long col = a.item_col[item];
+      const int ii = a.item_inst ? a.item_inst[item] : 0;
+      const bool ii_ok = !a.insts || (ii >= 0 && ii < a.ninst);
+      const int* lplanes = a.lplanes;
+      int nk = a.nk;
+      long long nxy = a.nxy, nrhs = (long long)a.nlp * a.nxy;
+      if (a.insts && ii_ok) {
+        const Inst& in = a.insts[ii];
+        lplanes = in.lplanes; nk = in.nk; nxy = in.g.nxy; nrhs = (long long)in.nlp * in.g.nxy;
+      }
+      st->inst = ii_ok ? ii : 0;
       st->item = item;
       st->it = 0;
       st->refresh = 0;
@@ -532,7 +590,7 @@ static __global__ void __launch_bounds__(1024) k_assign(const AssignArgs a) {
       st->res = 1.0;
       st->beta = make_double2(0.0, 0.0);
       st->rho = make_double2(a.H == 2 ? 2.0 : 1.0, 0.0);  // <e_j, e_j> in the pairing form
-      if (!isfinite(e) || ik < 0 || ik >= a.nk || col < 0 || col >= nrhs) {
+      if (!ii_ok || !isfinite(e) || ik < 0 || ik >= nk || col < 0 || col >= nrhs) {
         st->ik = 0;
         st->e = 0.0;
         st->j = 0;
@@ -541,7 +599,7 @@ static __global__ void __launch_bounds__(1024) k_assign(const AssignArgs a) {
       } else {
         st->ik = ik;
         st->e = e;
-        st->j = (long long)a.lplanes[col / a.nxy] * a.nxy + col % a.nxy;
+        st->j = (long long)lplanes[col / nxy] * nxy + col % nxy;
         st->result = 0;
         st->status = SLOT_ACTIVE;
         st->init = 1;
@@ -552,6 +610,18 @@ static __global__ void __launch_bounds__(1024) k_assign(const AssignArgs a) {
     __syncthreads();
   }
   if (tid == 0) a.queue->next = s_next;
+}
+
+// ---------------------------------------------------------------------------------
+// device-side loop control: ends the graph's WHILE loop once every item is harvested
+// or the per-launch chunk limit is reached (so a launch always ends)
+// ---------------------------------------------------------------------------------
+
+static __global__ void k_continue(cudaGraphConditionalHandle h, Queue* q) {
+  const int c = q->chunks + 1;
+  q->chunks = c;
+  const bool more = q->harvested < q->nitems && c < q->limit;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------------
@@ -567,6 +637,7 @@ struct InitArgs {
   const Slot* slots;
   long long n, slot_stride;
   int H;
+  const Inst* insts;
 };
 
 template <typename T>
@@ -575,12 +646,13 @@ __global__ void __launch_bounds__(256) k_init(const InitArgs<T> a) {
   const int slot = blockIdx.y;
   const Slot* st = a.slots + slot;
   if (!st->init) return;
+  const long long n = a.insts ? a.insts[st->inst].g.n : a.n;
   const long long j = st->j;
   const long long base = (long long)slot * a.slot_stride;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     for (int h = 0; h < a.H; ++h) {
-      const long long off = base + (long long)h * a.n + i;
+      const long long off = base + (long long)h * n + i;
       a.x[off] = czero<CT>();
       a.p[off] = czero<CT>();
       CT rv = czero<CT>();

@@ -42,6 +42,7 @@ static __global__ void __launch_bounds__(256) k_mx_prep(const MxPrepArgs a) {
     r.item = st.item;
     r.e = st.e;
     r.ik = st.ik;
+    r.inst = st.inst;
     r.j = st.j;
     r.beta = make_double2(0.0, 0.0);
   } else {
@@ -56,16 +57,18 @@ struct MxAccumArgs {
   const Slot* rslots;
   long long n, slot_stride;
   int H;
+  const Inst* insts;
 };
 
 static __global__ void __launch_bounds__(256) k_mx_accum(const MxAccumArgs a) {
   const int slot = blockIdx.y;
   if (a.rslots[slot].status != SLOT_ACTIVE) return;
+  const long long n = a.insts ? a.insts[a.rslots[slot].inst].g.n : a.n;
   const long long base = (long long)slot * a.slot_stride;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     for (int h = 0; h < a.H; ++h) {
-      const long long off = base + (long long)h * a.n + i;
+      const long long off = base + (long long)h * n + i;
       const float2 dv = a.d[off];
       double2 xv = a.x64[off];
       xv.x += (double)dv.x;
@@ -83,6 +86,7 @@ struct MxFinishArgs {
   double* part;  // [slot][gridDim.x][4]: rho re, rho im, |r_0|^2, |r_1|^2
   long long n, slot_stride;
   int H;
+  const Inst* insts;
 };
 
 static __global__ void __launch_bounds__(256) k_mx_finish(const MxFinishArgs a) {
@@ -91,13 +95,14 @@ static __global__ void __launch_bounds__(256) k_mx_finish(const MxFinishArgs a) 
   const Slot* st = a.rslots + slot;
   if (st->status != SLOT_ACTIVE) return;
   const long long j = st->j;
+  const long long n = a.insts ? a.insts[st->inst].g.n : a.n;
   const long long base = (long long)slot * a.slot_stride;
   double rrx = 0, rry = 0, n0 = 0, n1 = 0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     float2 rf[2];
     for (int h = 0; h < a.H; ++h) {
-      const long long off = base + (long long)h * a.n + i;
+      const long long off = base + (long long)h * n + i;
       const double2 q = a.q64[off];
       double2 r = make_double2(-q.x, -q.y);
       if (i == j) r.x += 1.0;
@@ -178,15 +183,17 @@ struct MxInitArgs {
   const Slot* slots;
   long long n, slot_stride;
   int H;
+  const Inst* insts;
 };
 
 static __global__ void __launch_bounds__(256) k_mx_init(const MxInitArgs a) {
   const int slot = blockIdx.y;
   if (!a.slots[slot].init) return;
+  const long long n = a.insts ? a.insts[a.slots[slot].inst].g.n : a.n;
   const long long base = (long long)slot * a.slot_stride;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
-    for (int h = 0; h < a.H; ++h) a.x64[base + (long long)h * a.n + i] = make_double2(0.0, 0.0);
+    for (int h = 0; h < a.H; ++h) a.x64[base + (long long)h * n + i] = make_double2(0.0, 0.0);
 }
 
 }  // namespace transec

@@ -147,3 +147,36 @@ def test_mixed_precision_free_electron_slab():
     assert np.all(out["status"] == 0), np.unique(out["status"], return_counts=True)
     assert np.abs(out["T"][:, 0] - ref).max() <= TOL_T
     assert fallbacks == 0, (fallbacks, out["iters"].max())
+
+
+def test_device_loop_matches_host_loop():
+    # one graph launch with a device-side WHILE loop must compute exactly what the
+    # host-polled chunk graphs compute
+    need_gpu()
+    inst = small_instance(6, 5, 28, 0.45, 10, 6, v_amp=0.8, kfrac=((0.27, -0.16),),
+                          energies=(0.42,), seed=21)
+    pos = np.arange(0, 120, 7, dtype=np.int64)
+    e = np.full(len(pos), 0.42)
+    ik = np.zeros(len(pos), np.int32)
+    with context(inst, slots=5, chunk=4) as tr:
+        dev = tr.column_contributions(e, ik, pos)
+        tr.set_solver(host_loop=1)
+        host = tr.column_contributions(e, ik, pos)
+    assert np.all(dev["status"] == 0)
+    assert np.array_equal(dev["t"], host["t"])
+    assert np.array_equal(dev["iters"], host["iters"])
+
+
+def test_autotune_picks_a_valid_shape():
+    need_gpu()
+    inst = small_instance(20, 20, 64, 0.341, 12, 8, v_amp=0.7, kfrac=((0.3125, -0.4375),),
+                          energies=(0.2,), seed=22)
+    with context(inst) as tr:
+        cfg = tr.autotune(0.2, 0)
+        o = tr.solver()
+        assert o["slab"] == cfg["slab"] and o["slots"] == cfg["slots"] and o["tile_y"] == cfg["tile_y"]
+        assert cfg["slab"] in (16, 32, 64, 128) and cfg["slots"] >= 1
+        r = tr.column_contributions(np.full(6, 0.2), np.zeros(6, np.int32), np.arange(6, dtype=np.int64) * 97)
+    _, tj = transmission_dense(inst.grid, inst.v, inst.gamma_l, inst.gamma_r, 0.2, inst.kfrac[0])
+    assert np.all(r["status"] == 0)
+    assert np.abs(r["t"] - tj[np.arange(6) * 97]).max() <= 1e-9

@@ -314,12 +314,15 @@ def rh_point_contact(instance: int = 0) -> Instance:
     )
 
 
-def uneven_batch(count: int = 96) -> list[Instance]:
+def uneven_batch(count: int = 96, only=None) -> list[Instance]:
     """Seeded mix of Cu/Rh bulk and point-contact cells of uneven size: lateral cells
     1x1..4x4 conventional cells, 12-40 cells long, h in [0.30, 0.40] bohr, 1-16
-    k-points and 64-512 energies per instance."""
+    k-points and 64-512 energies per instance.  ``only`` builds just the listed
+    instance indices (each instance depends only on its own seed)."""
     out = []
     for i in range(count):
+        if only is not None and i not in only:
+            continue
         seed = config_seed(4, i)
         rng = np.random.default_rng(seed)
         metal = "Cu" if rng.random() < 0.5 else "Rh"
