@@ -195,6 +195,72 @@ def run_reference(args):
     return 0
 
 
+def run_uneven_batch(args):
+    """Configuration 4: 96 seeded Cu/Rh bulk and point-contact cells of uneven size.
+    A step takes one seeded (E at mid-window, k, column) item from each of 16 seeded
+    cells and solves them together in one batched launch (one slot engine, the cells'
+    operators in a table); the same items solved one cell at a time give the looped
+    figure.  Reports column-solves/s of both and their ratio."""
+    import torch
+
+    from workloads import uneven_batch
+    import paper_2208_02783_gb300 as pkg
+    from paper_2208_02783_gb300 import build
+
+    pkg.load(build.build())
+    prec = pkg.PREC_MIXED if args.form == "mixed" else pkg.PREC_FP64
+    insts = uneven_batch(96)
+    ctxs = [pkg.Transec.from_instance(i, device=0, tol=1e-10, precision=prec) for i in insts]
+    per_step = 16
+
+    def items(step):
+        rng = np.random.default_rng(4000 + step)
+        cells = rng.choice(len(insts), per_step, replace=False)
+        e = np.array([insts[c].energies[len(insts[c].energies) // 2] for c in cells])
+        k = np.array([rng.integers(0, len(insts[c].kfrac)) for c in cells], np.int32)
+        col = np.array([rng.integers(0, insts[c].n_rhs) for c in cells], np.int64)
+        return cells.astype(np.int32), e, k, col
+
+    for s in range(args.warmup):
+        cells, e, k, col = items(s)
+        pkg.batch_column_contributions(ctxs, cells, e, k, col)
+    torch.cuda.synchronize()
+    t_batch = 0.0
+    t_loop = 0.0
+    its = 0
+    fails = 0
+    for s in range(args.steps):
+        cells, e, k, col = items(args.warmup + s)
+        t0 = time.perf_counter()
+        r = pkg.batch_column_contributions(ctxs, cells, e, k, col)
+        t_batch += time.perf_counter() - t0
+        its += int(r["iters"].sum())
+        fails += int((r["status"] != 0).sum())
+        t0 = time.perf_counter()
+        for u, c in enumerate(cells):
+            q = ctxs[c].column_contributions(e[u:u + 1], k[u:u + 1], col[u:u + 1])
+            if q["status"][0] != 0 or abs(q["t"][0] - r["t"][u]) > 1e-6 / 25600:
+                fails += 1
+        t_loop += time.perf_counter() - t0
+    n = per_step * args.steps
+    line = {
+        "metric": "uneven batch column-solves/s (batched one launch vs looped per cell)",
+        "value": n / t_batch, "unit": "column-solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128" if prec == pkg.PREC_FP64 else "c64+f64",
+        "data": "synthetic",
+        "config": {"workload": "96 seeded Cu/Rh bulk and point-contact cells, 1x1-4x4 cells wide, "
+                               "12-40 cells long, h 0.30-0.40, order 12 (configuration 4)",
+                   "items_per_step": per_step, "looped_column_solves_per_s": n / t_loop,
+                   "batched_over_looped": t_loop / t_batch, "mean_iterations": its / n,
+                   "mismatched_or_failed": fails},
+    }
+    print(json.dumps(line))
+    for c in ctxs:
+        c.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,9 +273,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="small bounded run for ncu: 32 columns, 40 iterations each, then exit")
+    ap.add_argument("--workload", default="cu_bulk", choices=["cu_bulk", "uneven_batch"],
+                    help="uneven_batch: the 96-cell mixed batch, batched vs looped per cell")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven_batch":
+        return run_uneven_batch(args)
 
     import torch
     import torch.distributed as dist
