@@ -37,6 +37,11 @@ UNIT = "(E,k) solves/s"
 WORKLOAD = ("bulk fcc Cu [001] a=6.82, 20x20x480 h=0.341, order 12, V0=1.2 sigma=0.9 +-2% "
             "jitter, 64-plane CAPs 0.3 Ha, 8x8 MP k-mesh, 256 energies in E_F+-0.3 Ha, tol 1e-10")
 HBM_FALLBACK_GBS = 6800.0
+# DRAM bytes per point-half of one FP64 stencil launch, from the ncu capture in
+# profiles/k_stencil_fp64_cu_bulk.md (897.7 MB for 12.29 M point-halves); scaled by the
+# point-halves of each launch for the roofline's traffic.  Reset to None whenever the
+# kernel changes.
+FP64_STENCIL_DRAM_PER_POINT_HALF = 897.7e6 / 12.288e6
 # FP64 ALU roofline: 2 FP64 FMA per clock per SM x 152 SMs x 2070 MHz x 2 flops
 FP64_PEAK_TFLOPS = 2 * 152 * 2.070e9 * 2 / 1e12
 
@@ -416,7 +421,9 @@ def main():
     if prec == pkg.PREC_FP64:
         achieved = flops / sten_s / 1e12 if sten_s > 0 else 0.0
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": (FP64_STENCIL_DRAM_PER_POINT_HALF * pa / launches_s
+                            if FP64_STENCIL_DRAM_PER_POINT_HALF else None),
                 "kernel": "k_stencil<double,6> (FP64 stencil fused with p = r + beta p and the pairing dot)",
                 "per_launch": {"flops": flops / launches_s, "bytes": bytes_alg / launches_s,
                                "ms": st["stencil_ms"] / launches_s},
