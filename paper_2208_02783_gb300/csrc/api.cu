@@ -294,6 +294,8 @@ BatchPlan plan_batch(const transec_ctx* driver, const std::vector<transec_ctx*>&
     in.gl = m->d_gl;
     in.gr = m->d_gr;
     in.phase = m->d_phase;
+    in.gam32 = m->d_gam32;
+    in.phase32 = m->d_phase32;
     in.lplanes = m->d_lplanes;
     in.rplanes = m->d_rplanes;
     in.nlp = (int)m->lplanes.size();
@@ -906,9 +908,10 @@ int transec_set_abc(transec_ctx* ctx, const double* gamma_l, const double* gamma
   }
   if (lp.empty()) return fail(ctx, TRANSEC_EINVAL, "left absorbing profile is zero everywhere");
   DeviceGuard dg(ctx->device);
-  cudaFree(ctx->d_gl); cudaFree(ctx->d_gr); cudaFree(ctx->d_gam);
+  cudaFree(ctx->d_gl); cudaFree(ctx->d_gr); cudaFree(ctx->d_gam); cudaFree(ctx->d_gam32);
   cudaFree(ctx->d_lplanes); cudaFree(ctx->d_rplanes);
   ctx->d_gl = ctx->d_gr = ctx->d_gam = nullptr;
+  ctx->d_gam32 = nullptr;
   ctx->d_lplanes = ctx->d_rplanes = nullptr;
   ctx->have_abc = false;
   CK(cudaMalloc(&ctx->d_gl, nz * sizeof(double)));
@@ -919,6 +922,11 @@ int transec_set_abc(transec_ctx* ctx, const double* gamma_l, const double* gamma
   CK(cudaMemcpy(ctx->d_gl, gamma_l, nz * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_gr, gamma_r, nz * sizeof(double), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_gam, gam.data(), nz * sizeof(double), cudaMemcpyHostToDevice));
+  {
+    std::vector<float> g32(gam.begin(), gam.end());
+    CK(cudaMalloc(&ctx->d_gam32, nz * sizeof(float)));
+    CK(cudaMemcpy(ctx->d_gam32, g32.data(), nz * sizeof(float), cudaMemcpyHostToDevice));
+  }
   CK(cudaMemcpy(ctx->d_lplanes, lp.data(), lp.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (!rp.empty())
     CK(cudaMemcpy(ctx->d_rplanes, rp.data(), rp.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -953,10 +961,18 @@ int transec_set_kmesh(transec_ctx* ctx, int nk, const double* kfrac, const doubl
         }
   DeviceGuard dg(ctx->device);
   cudaFree(ctx->d_phase);
+  cudaFree(ctx->d_phase32);
   ctx->d_phase = nullptr;
+  ctx->d_phase32 = nullptr;
   ctx->have_k = false;
   CK(cudaMalloc(&ctx->d_phase, tab.size() * sizeof(double2)));
   CK(cudaMemcpy(ctx->d_phase, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  {
+    std::vector<float2> t32(tab.size());
+    for (size_t u = 0; u < tab.size(); ++u) t32[u] = make_float2((float)tab[u].x, (float)tab[u].y);
+    CK(cudaMalloc(&ctx->d_phase32, t32.size() * sizeof(float2)));
+    CK(cudaMemcpy(ctx->d_phase32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   ctx->nk = nk;
   ctx->kfrac.assign(kfrac, kfrac + 2 * nk);
   ctx->kw = w;
@@ -1419,6 +1435,7 @@ void transec_destroy(transec_ctx* ctx) {
   cudaFree(ctx->d_v); cudaFree(ctx->d_v32);
   cudaFree(ctx->d_gl); cudaFree(ctx->d_gr); cudaFree(ctx->d_gam);
   cudaFree(ctx->d_lplanes); cudaFree(ctx->d_rplanes); cudaFree(ctx->d_phase);
+  cudaFree(ctx->d_gam32); cudaFree(ctx->d_phase32);
   if (ctx->h_harvest) cudaFreeHost(ctx->h_harvest);
   for (cudaEvent_t e : ctx->prof_ev) cudaEventDestroy(e);
   if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);

@@ -52,6 +52,8 @@ struct Inst {
   const int* rplanes;    // planes with Gamma_R > 0
   int nlp, nrp, nk, pad;
   TileShape tile[2];
+  const float* gam32;    // FP32 copies for the FP32 stencil (no conversions per point)
+  const float2* phase32;
 };
 
 // Per-slot solver state (device resident).

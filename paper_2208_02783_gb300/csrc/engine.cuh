@@ -62,6 +62,7 @@ struct transec_ctx {
   double* d_gl = nullptr;
   double* d_gr = nullptr;
   double* d_gam = nullptr;
+  float* d_gam32 = nullptr;
   int* d_lplanes = nullptr;
   int* d_rplanes = nullptr;
   std::vector<int> lplanes, rplanes;
@@ -69,6 +70,7 @@ struct transec_ctx {
   int nk = 0;
   std::vector<double> kfrac, kw;
   double2* d_phase = nullptr;
+  float2* d_phase32 = nullptr;
   bool have_k = false;
   transec_solver_opts opts{};
   std::string err;

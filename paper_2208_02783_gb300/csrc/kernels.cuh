@@ -127,17 +127,34 @@ struct StencilArgs {
 template <typename T> __device__ inline const T* inst_potential(const Inst& in);
 template <> __device__ inline const double* inst_potential<double>(const Inst& in) { return in.v; }
 template <> __device__ inline const float* inst_potential<float>(const Inst& in) { return in.v32; }
+// Gamma profile and Bloch phase table in the arithmetic type of the kernel
+template <typename T> __device__ inline const T* inst_gamma(const Inst& in);
+template <> __device__ inline const double* inst_gamma<double>(const Inst& in) { return in.gam; }
+template <> __device__ inline const float* inst_gamma<float>(const Inst& in) { return in.gam32; }
+template <typename T> __device__ inline const typename Cx<T>::type* inst_phase(const Inst& in);
+template <> __device__ inline const double2* inst_phase<double>(const Inst& in) { return in.phase; }
+template <> __device__ inline const float2* inst_phase<float>(const Inst& in) { return in.phase32; }
+// argument-mode tables (the stand-alone apply paths run in FP64 only)
+template <typename T> __device__ inline const T* args_gamma(const double* g);
+template <> __device__ inline const double* args_gamma<double>(const double* g) { return g; }
+template <> __device__ inline const float* args_gamma<float>(const double*) { return nullptr; }
+template <typename T> __device__ inline const typename Cx<T>::type* args_phase(const double2* p);
+template <> __device__ inline const double2* args_phase<double>(const double2* p) { return p; }
+template <> __device__ inline const float2* args_phase<float>(const double2*) { return nullptr; }
 
 // Block = TX*TY*H threads (rounded up to whole warps), one grid point (x, y) per thread and half, marching over
 // the z-slab [z0, z0 + D) with a register queue of the 2R+1 planes around the
 // centre plane; the centre plane (plus lateral halos, Bloch-phased when wrapped)
 // sits in shared memory for the x/y neighbours.  Grid = (tiles, slabs, slots).
-// Threads per stencil block: FP64 keeps the 13-plane queue in 128 registers.
-template <typename T> struct StencilMax { static constexpr int threads = 768; };
-template <> struct StencilMax<double> { static constexpr int threads = 512; };
+// Threads per stencil block: FP64 keeps the 13-plane queue in 128 registers (one
+// block per SM); FP32 is held to 64 registers so that two blocks share an SM, since
+// the HBM-bound FP32 kernel needs the warps to cover its per-plane loads.
+template <typename T> struct StencilMax { static constexpr int threads = 512, blocks = 2; };
+template <> struct StencilMax<double> { static constexpr int threads = 448, blocks = 1; };
 
 template <typename T, int R>
-__global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const StencilArgs<T> a) {
+__global__ void __launch_bounds__(StencilMax<T>::threads, StencilMax<T>::blocks)
+    k_stencil(const StencilArgs<T> a) {
   using CT = typename Cx<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2][32];
@@ -153,16 +170,16 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
   // operator and launch shape: kernel arguments, or the slot's batch entry
   const Geometry* gp = &a.g;
   const T* vp = a.v;
-  const double* gamp = a.gam;
-  const double2* phase = a.phase;
+  const T* gamp = args_gamma<T>(a.gam);
+  const CT* phase = args_phase<T>(a.phase);
   int TX = a.TX, TY = a.TY, D = a.D, ntx = a.ntx;
   bool beyond = false;
   if (a.insts) {
     const Inst& in = a.insts[stp->inst];
     gp = &in.g;
     vp = inst_potential<T>(in);
-    gamp = in.gam;
-    phase = in.phase;
+    gamp = inst_gamma<T>(in);
+    phase = inst_phase<T>(in);
     const TileShape& ts = in.tile[a.tile_idx];
     TX = ts.TX; TY = ts.TY; D = ts.D; ntx = ts.ntx;
     beyond = (int)blockIdx.x >= ts.ntx * ts.nty || (int)blockIdx.y >= ts.nslab;
@@ -199,7 +216,7 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
   CT* __restrict__ pout = a.p_out + base;
   CT* __restrict__ q = a.q + base;
   const CT beta = cfrom<CT>(beta_d);
-  const double2* ph = phase + (size_t)(ik * 2 + (half ^ a.conj)) * 2 * kPhaseN;
+  const CT* ph = phase + (size_t)(ik * 2 + (half ^ a.conj)) * 2 * kPhaseN;
   const long long pidx = (long long)gx + (long long)nx * gy;
 
   T kx[R + 1], ky[R + 1], kz[R + 1];
@@ -225,8 +242,8 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
     if (xx < 0 || xx >= nx) { wx = floordiv(xx, nx); xx -= wx * nx; }
     if (yy < 0 || yy >= ny) { wy = floordiv(yy, ny); yy -= wy * ny; }
     CT v = pnew((long long)zc * nxy + xx + (long long)nx * yy);
-    if (wx) v = cmul(v, cfrom<CT>(ph[kPhaseW + wx]));
-    if (wy) v = cmul(v, cfrom<CT>(ph[kPhaseN + kPhaseW + wy]));
+    if (wx) v = cmul(v, ph[kPhaseW + wx]);
+    if (wy) v = cmul(v, ph[kPhaseN + kPhaseW + wy]);
     return v;
   };
 
@@ -267,7 +284,7 @@ __global__ void __launch_bounds__(StencilMax<T>::threads) k_stencil(const Stenci
     if (inside) {
       const long long off = (long long)zc * nxy + pidx;
       const T dr = ediag - vp[off];
-      const T di = (T)gamp[zc];
+      const T di = gamp[zc];
       CT acc;
       acc.x = dr * c.x - di * c.y;
       acc.y = dr * c.y + di * c.x;
