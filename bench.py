@@ -420,11 +420,13 @@ def main():
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     elem = 16 if prec == pkg.PREC_FP64 else 8
-    pa = st["point_applies"]
-    sten_s = st["stencil_ms"] / 1e3
+    if prec == pkg.PREC_FP64:
+        pa, sten_s, launches_s = st["point_applies"], st["stencil_ms"] / 1e3, st["stencil_launches"]
+    else:  # the FP32 stencil of the mixed form (fallback FP64 work is counted apart)
+        pa, sten_s, launches_s = st["point_applies32"], st["stencil32_ms"] / 1e3, st["stencil32_launches"]
+    launches_s = max(1, launches_s)
     flops = pa * stencil_flops_per_point(g.order)
     bytes_alg = pa * stencil_bytes_per_point(elem)
-    launches_s = max(1, st["stencil_launches"])
     if prec == pkg.PREC_FP64:
         achieved = flops / sten_s / 1e12 if sten_s > 0 else 0.0
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -89,6 +89,10 @@ typedef struct transec_solver_opts {
   int mixed_maxit;    /* mixed precision: FP32 iterations a column may take before it is
                          handed to the plain FP64 engine (solved again from scratch);
                          default 8000 */
+  int mixed_decade_its; /* mixed precision: a column whose FP32 residual has fallen by less
+                         than one decade per this many iterations (checked from that many
+                         iterations on) is handed to the FP64 engine; default 1000,
+                         negative = never */
   int host_loop;      /* 0 (default): the whole solve is one CUDA-graph launch whose
                          device-side WHILE loop runs chunk after chunk until the queue is
                          drained (bounded by maxit); != 0: the host launches and polls one
@@ -243,11 +247,14 @@ int transec_trace(transec_ctx* ctx, int nvec, const double* x, const int64_t* co
  * opts.profile set, stencil_ms / update_ms = summed device time of the stencil and
  * vector-update launches and stencil_launches / update_launches their counts;
  * fallbacks = mixed-precision columns that did not converge in the mixed form and
- * were solved again by the plain FP64 engine.  Any output pointer may be NULL.
+ * were solved again by the plain FP64 engine.  point_applies / stencil_ms /
+ * stencil_launches count the FP64 kernels; point_applies32 / stencil32_ms /
+ * stencil32_launches the FP32 kernels of the mixed form.  Any output may be NULL.
  */
 int transec_stats(const transec_ctx* ctx, long long* launches, long long* point_applies,
                   double* stencil_ms, long long* stencil_launches, double* update_ms,
-                  long long* update_launches, long long* fallbacks);
+                  long long* update_launches, long long* fallbacks, long long* point_applies32,
+                  double* stencil32_ms, long long* stencil32_launches);
 int transec_stats_reset(transec_ctx* ctx);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next

@@ -47,6 +47,7 @@ class SolverOpts(C.Structure):
         ("slab", C.c_int),
         ("profile", C.c_int),
         ("mixed_maxit", C.c_int),
+        ("mixed_decade_its", C.c_int),
         ("host_loop", C.c_int),
     ]
 
@@ -79,7 +80,8 @@ _SIGS = {
     "transec_stats": (C.c_int, [_P] + [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double), C.POINTER(C.c_longlong),
-                                        C.POINTER(C.c_longlong)]),
+                                        C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                        C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "transec_stats_reset": (C.c_int, [_P]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
@@ -329,10 +331,10 @@ def transec_trace(ctx, x, cols, t_out):
 
 def transec_stats(ctx) -> dict:
     v = [C.c_longlong(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(),
-         C.c_longlong()]
+         C.c_longlong(), C.c_longlong(), C.c_double(), C.c_longlong()]
     _check(ctx, load().transec_stats(ctx, *[C.byref(x) for x in v]), "transec_stats")
     keys = ("launches", "point_applies", "stencil_ms", "stencil_launches", "update_ms", "update_launches",
-            "fallbacks")
+            "fallbacks", "point_applies32", "stencil32_ms", "stencil32_launches")
     return {k: x.value for k, x in zip(keys, v)}
 
 

@@ -94,6 +94,7 @@ void default_opts(transec_solver_opts* o) {
   if (o->chunk % 2) o->chunk += 1;  // the p ping-pong must end where it started
   if (o->reliable <= 0 || o->reliable >= 1) o->reliable = 1e-5;
   if (o->mixed_maxit <= 0) o->mixed_maxit = 8000;
+  if (o->mixed_decade_its == 0) o->mixed_decade_its = 1000;
 }
 
 // Bloch phase exp(2 pi i kappa w) with the argument reduced before the cosine.
@@ -331,12 +332,17 @@ int ensure_events(transec_ctx* ctx, int n) {
   return TRANSEC_OK;
 }
 
-void accumulate_events(transec_ctx* ctx, int C) {
+void accumulate_events(transec_ctx* ctx, int C, bool fp32) {
   for (int i = 0; i < C; ++i) {
     float a = 0.f, b = 0.f;
     if (cudaEventElapsedTime(&a, ctx->prof_ev[4 * i], ctx->prof_ev[4 * i + 1]) == cudaSuccess) {
-      ctx->stencil_ms += a;
-      ctx->stencil_launches += 1;
+      if (fp32) {
+        ctx->stencil32_ms += a;
+        ctx->stencil32_launches += 1;
+      } else {
+        ctx->stencil_ms += a;
+        ctx->stencil_launches += 1;
+      }
     }
     if (cudaEventElapsedTime(&b, ctx->prof_ev[4 * i + 2], ctx->prof_ev[4 * i + 3]) == cudaSuccess) {
       ctx->update_ms += b;
@@ -456,6 +462,7 @@ int run_engine(transec_ctx* ctx, const std::vector<transec_ctx*>& members, const
   // thousands of iterations before they fall, and a restart there loses the progress)
   ca.mixed = mixed ? 1 : 0; ca.reliable = ctx->opts.reliable; ca.stall = 1 << 30;
   ca.max_gap = 1 << 30;
+  ca.decade_its = mixed ? ctx->opts.mixed_decade_its : 0;
   const int cgrid = (aa.S + 7) / 8;
 
   // the trace reads the FP64 solution: the engine's x (plain) or x64 (mixed)
@@ -594,7 +601,7 @@ int run_engine(transec_ctx* ctx, const std::vector<transec_ctx*>& members, const
       rcode = fail(ctx, TRANSEC_ECUDA, std::string("solver chunk: ") + cudaGetErrorString(e3));
       break;
     }
-    if (prof) accumulate_events(ctx, C);
+    if (prof) accumulate_events(ctx, C, !std::is_same<T, double>::value);
     if (*ctx->h_harvest >= nitems) break;
     if (chunks > max_chunks) {
       rcode = fail(ctx, TRANSEC_ETIMEOUT, "solver did not drain its work queue within the iteration bound");
@@ -610,7 +617,9 @@ int run_engine(transec_ctx* ctx, const std::vector<transec_ctx*>& members, const
     if (ok) {
       for (int i = 0; i < nitems; ++i) {
         const int ii = (inst[i] >= 0 && inst[i] < ninst) ? inst[i] : 0;
-        ctx->point_applies += (long long)its[i] * H * bp.insts[ii].g.n;
+        const long long pa = (long long)its[i] * H * bp.insts[ii].g.n;
+        if (std::is_same<T, double>::value) ctx->point_applies += pa;
+        else ctx->point_applies32 += pa;
       }
     }
     cudaGetLastError();
@@ -1193,9 +1202,9 @@ int transec_autotune(transec_ctx* ctx, double energy, int ik, int* tile_y_out, i
           ctx->opts = saved;
           return rc;
         }
-        const double ms = ctx->stencil_ms + ctx->update_ms;
-        // the fallback re-solve of the mixed form is not part of the candidate's rate
-        const double rate = ms > 0 ? (double)ctx->point_applies / ms : 0.0;
+        const double ms = ctx->stencil_ms + ctx->stencil32_ms + ctx->update_ms;
+        const double rate =
+            ms > 0 ? (double)(ctx->point_applies + ctx->point_applies32) / ms : 0.0;
         if (rate > best) {
           best = rate;
           by = ty;
@@ -1399,9 +1408,13 @@ int transec_trace(transec_ctx* ctx, int nvec, const double* x, const int64_t* co
 
 int transec_stats(const transec_ctx* ctx, long long* launches, long long* point_applies,
                   double* stencil_ms, long long* stencil_launches, double* update_ms,
-                  long long* update_launches, long long* fallbacks) {
+                  long long* update_launches, long long* fallbacks, long long* point_applies32,
+                  double* stencil32_ms, long long* stencil32_launches) {
   if (!ctx) return TRANSEC_EINVAL;
   if (fallbacks) *fallbacks = ctx->fallbacks;
+  if (point_applies32) *point_applies32 = ctx->point_applies32;
+  if (stencil32_ms) *stencil32_ms = ctx->stencil32_ms;
+  if (stencil32_launches) *stencil32_launches = ctx->stencil32_launches;
   if (launches) *launches = ctx->launches;
   if (point_applies) *point_applies = ctx->point_applies;
   if (stencil_ms) *stencil_ms = ctx->stencil_ms;
@@ -1418,6 +1431,8 @@ int transec_stats_reset(transec_ctx* ctx) {
   ctx->stencil_ms = ctx->update_ms = 0;
   ctx->stencil_launches = ctx->update_launches = 0;
   ctx->fallbacks = 0;
+  ctx->stencil32_ms = 0;
+  ctx->stencil32_launches = ctx->point_applies32 = 0;
   return TRANSEC_OK;
 }
 

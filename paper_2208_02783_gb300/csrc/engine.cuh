@@ -100,5 +100,9 @@ struct transec_ctx {
   double stencil_ms = 0, update_ms = 0;
   long long stencil_launches = 0, update_launches = 0;
   long long fallbacks = 0;  // mixed-precision columns re-solved in FP64
+  // the same for the FP32 kernels of the mixed form (the FP64 fields then hold the
+  // residual replacements' and fallbacks' FP64 work only)
+  double stencil32_ms = 0;
+  long long stencil32_launches = 0, point_applies32 = 0;
   std::vector<cudaEvent_t> prof_ev;  // 4 per iteration of a chunk when profiling
 };

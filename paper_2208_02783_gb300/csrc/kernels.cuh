@@ -413,6 +413,8 @@ struct ScalarArgs {
   double reliable;         // replacement when the residual dropped by this factor,
   int stall;               // ... or found no new minimum for this many iterations,
   int max_gap;             // ... or after this many iterations without one
+  int decade_its;          // mixed: give up (ENOCONV, FP64 fallback) once the residual
+                           // has fallen by less than one decade per this many iterations
 };
 
 // Status codes written to Slot::result (same values as the C ABI).
@@ -456,6 +458,13 @@ static __global__ void __launch_bounds__(256) k_scalars(const ScalarArgs a) {
       if (res <= a.reliable * st->rmax || res <= a.tol || it - st->it_best >= a.stall ||
           it - st->last_ref >= a.max_gap)
         st->pending = 1;
+      // the FP32 iteration stagnates on the hard columns (FP32 rounding of the search
+      // directions, amplified by the high end of the spectrum); hand them over early
+      if (a.decade_its > 0 && it >= a.decade_its &&
+          fmin(st->rbest, st->rmax) > exp10(-(double)it / a.decade_its)) {
+        st->result = kENOCONV;
+        st->status = SLOT_DONE;
+      }
     }
   }
 }
