@@ -257,6 +257,38 @@ int transec_stats(const transec_ctx* ctx, long long* launches, long long* point_
                   double* stencil32_ms, long long* stencil32_launches);
 int transec_stats_reset(transec_ctx* ctx);
 
+/*
+ * Learned right preconditioner (NS growth; the paper has no learned component): a
+ * 3D U-Net with 3 levels of 16/32/64 channels, 3x3x3 convolutions (zero padding),
+ * ReLU, 2x2x2 average pooling, nearest 2x upsampling and skip concatenation, 4 input
+ * channels (Re r, Im r, V, Gamma) and 2 outputs (Re e, Im e).  Its convolutions run as
+ * BF16 tensor-core implicit GEMMs with FP32 accumulation (forward, data gradient,
+ * weight gradient), trained with Adam on FP32 master weights.  A network is built for
+ * one volume nx x ny x nz (each a multiple of 4).
+ */
+typedef struct transec_unet transec_unet;
+
+/* Create a network with He-initialised weights from `seed`.  Errors: EINVAL (sizes),
+ * ENOMEM, ECUDA. */
+int transec_unet_create(transec_unet** out, int device, int nx, int ny, int nz,
+                        unsigned long long seed);
+/* Parameter count and flat FP32 parameters in host memory: per layer (e1a, e1b, e2a,
+ * e2b, e3a, e3b, d2a, d2b, d1a, d1b, out) the weights (27, cout, cin) then the bias
+ * (cout).  set_params(NULL) only resets the optimiser state. */
+int transec_unet_n_params(const transec_unet* u, long long* n);
+int transec_unet_set_params(transec_unet* u, const float* params);
+int transec_unet_get_params(transec_unet* u, float* params);
+/* out[v][0..1] = network(in[v][0..3]) for every voxel v = x + nx(y + ny z); FP32, device
+ * (on_device != 0) or host memory. */
+int transec_unet_forward(transec_unet* u, const float* in, float* out, int on_device);
+/* One training step on one volume: relative loss sum|y - t|^2 / sum|t|^2 against
+ * target[v][0..1], backward, and an Adam update when lr > 0.  loss / grads (host, flat
+ * layout) may be NULL.  Device or host arrays. */
+int transec_unet_train_step(transec_unet* u, const float* in, const float* target, float lr,
+                            float* loss, float* grads, int on_device);
+const char* transec_unet_last_error(const transec_unet* u);
+void transec_unet_destroy(transec_unet* u);
+
 /* Message of the last failure on this context ("" if none).  Valid until the next
  * call on the same context. */
 const char* transec_last_error(const transec_ctx* ctx);

@@ -83,6 +83,14 @@ _SIGS = {
                                         C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                         C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "transec_stats_reset": (C.c_int, [_P]),
+    "transec_unet_create": (C.c_int, [C.POINTER(_P), C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong]),
+    "transec_unet_n_params": (C.c_int, [_P, C.POINTER(C.c_longlong)]),
+    "transec_unet_set_params": (C.c_int, [_P, _P]),
+    "transec_unet_get_params": (C.c_int, [_P, _P]),
+    "transec_unet_forward": (C.c_int, [_P, _P, _P, C.c_int]),
+    "transec_unet_train_step": (C.c_int, [_P, _P, _P, C.c_float, C.POINTER(C.c_float), _P, C.c_int]),
+    "transec_unet_last_error": (C.c_char_p, [_P]),
+    "transec_unet_destroy": (None, [_P]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
 }
@@ -133,7 +141,8 @@ class _Arr:
         except ImportError:  # pragma: no cover
             is_torch = False
         if is_torch:
-            tdt = {np.float64: "torch.float64", np.int32: "torch.int32", np.int64: "torch.int64"}[dtype]
+            tdt = {np.float64: "torch.float64", np.int32: "torch.int32", np.int64: "torch.int64",
+                   np.float32: "torch.float32"}[dtype]
             if str(a.dtype) != tdt:
                 raise TypeError(f"expected {tdt}, got {a.dtype}")
             if not a.is_contiguous():
@@ -358,3 +367,61 @@ _NPOINTS: dict[int, int] = {}
 
 def transec_n_points(ctx) -> int:
     return _NPOINTS[ctx.value]
+
+
+# ----------------------------------------------------------------------------------
+# the learned preconditioner's network
+# ----------------------------------------------------------------------------------
+
+
+def _ucheck(u, st, what):
+    if st != OK:
+        lib = load()
+        raise TransecError(st, f"{what}: {lib.transec_status_string(st).decode()}: "
+                               f"{lib.transec_unet_last_error(u).decode() if u else ''}")
+
+
+def transec_unet_create(device, nx, ny, nz, seed=0):
+    out = C.c_void_p()
+    _ucheck(None, load().transec_unet_create(C.byref(out), device, nx, ny, nz, seed), "transec_unet_create")
+    return out
+
+
+def transec_unet_n_params(u) -> int:
+    n = C.c_longlong()
+    _ucheck(u, load().transec_unet_n_params(u, C.byref(n)), "transec_unet_n_params")
+    return int(n.value)
+
+
+def transec_unet_set_params(u, params):
+    a = _Arr(np.asarray(params, np.float32), np.float32) if params is not None else None
+    _ucheck(u, load().transec_unet_set_params(u, a.ptr if a else None), "transec_unet_set_params")
+
+
+def transec_unet_get_params(u):
+    out = np.zeros(transec_unet_n_params(u), np.float32)
+    _ucheck(u, load().transec_unet_get_params(u, out.ctypes.data_as(C.c_void_p)), "transec_unet_get_params")
+    return out
+
+
+def transec_unet_forward(u, x, y):
+    a = _Arr(x, np.float32)
+    b = _Arr(y, np.float32, writable=True)
+    _ucheck(u, load().transec_unet_forward(u, a.ptr, b.ptr, _side([a, b])), "transec_unet_forward")
+
+
+def transec_unet_train_step(u, x, target, lr, want_grads=False):
+    a = _Arr(x, np.float32)
+    t = _Arr(target, np.float32)
+    loss = C.c_float()
+    grads = np.zeros(transec_unet_n_params(u), np.float32) if want_grads else None
+    st = load().transec_unet_train_step(u, a.ptr, t.ptr, float(lr), C.byref(loss),
+                                        grads.ctypes.data_as(C.c_void_p) if want_grads else None,
+                                        _side([a, t]))
+    _ucheck(u, st, "transec_unet_train_step")
+    return float(loss.value), grads
+
+
+def transec_unet_destroy(u):
+    if u:
+        load().transec_unet_destroy(u)

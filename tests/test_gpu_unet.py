@@ -1,0 +1,95 @@
+"""The learned preconditioner's network on the GPU against the NumPy reference.
+
+The GPU runs BF16 tensor-core convolutions with FP32 accumulation, so values and
+gradients are compared by relative L2 error, with bars that BF16 storage of the
+activations (8 significant bits) and of the gradients fixes: 3e-2 for the output, 6e-2
+for each parameter gradient.  The reference itself is pinned by finite differences in
+tests/test_oracle_unet.py.
+"""
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import library, need_gpu
+from oracle import unet as ref
+
+pytestmark = pytest.mark.gpu
+
+SHAPE = (8, 8, 16)  # nz, ny, nx
+
+
+def _unflatten(flat):
+    p, q = {}, 0
+    for name, cin, cout, _ in ref.LAYERS:
+        n = 27 * cout * cin
+        p[name + ".w"] = flat[q:q + n].reshape(27, cout, cin).astype(np.float64)
+        q += n
+        p[name + ".b"] = flat[q:q + cout].astype(np.float64)
+        q += cout
+    return p
+
+
+def _flatten(g):
+    return np.concatenate([np.concatenate([g[n + ".w"].ravel(), g[n + ".b"]]) for n, *_ in ref.LAYERS])
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def _setup(pkg, seed=5):
+    nz, ny, nx = SHAPE
+    u = pkg.binding.transec_unet_create(0, nx, ny, nz, seed)
+    rng = np.random.default_rng(seed)
+    x = rng.normal(size=SHAPE + (4,)).astype(np.float32)
+    t = rng.normal(size=SHAPE + (2,)).astype(np.float32)
+    # biases are zero at initialisation; give them values so that they are tested too
+    flat = pkg.binding.transec_unet_get_params(u)
+    params = _unflatten(flat)
+    for name, *_ in ref.LAYERS:
+        params[name + ".b"] = rng.normal(0, 0.05, params[name + ".b"].shape)
+    pkg.binding.transec_unet_set_params(u, _flatten(params).astype(np.float32))
+    params = _unflatten(pkg.binding.transec_unet_get_params(u))
+    return u, x, t, params
+
+
+def test_forward_matches_reference():
+    need_gpu()
+    pkg = library()
+    u, x, t, params = _setup(pkg)
+    try:
+        y = np.zeros(SHAPE + (2,), np.float32)
+        pkg.binding.transec_unet_forward(u, x, y)
+        yr, _ = ref.forward(params, x.astype(np.float64))
+        assert _rel(y, yr) <= 3e-2
+    finally:
+        pkg.binding.transec_unet_destroy(u)
+
+
+def test_gradients_match_reference():
+    need_gpu()
+    pkg = library()
+    u, x, t, params = _setup(pkg, seed=6)
+    try:
+        loss, g = pkg.binding.transec_unet_train_step(u, x, t, 0.0, want_grads=True)
+        yr, cache = ref.forward(params, x.astype(np.float64))
+        lr, dy = ref.relative_loss(yr, t.astype(np.float64))
+        gr = ref.backward(params, cache, dy)
+        assert abs(loss - lr) <= 3e-2 * lr
+        gg = _unflatten(g)
+        for name, *_ in ref.LAYERS:
+            for suffix in (".w", ".b"):
+                assert _rel(gg[name + suffix], gr[name + suffix]) <= 6e-2, name + suffix
+    finally:
+        pkg.binding.transec_unet_destroy(u)
+
+
+def test_training_reduces_loss():
+    need_gpu()
+    pkg = library()
+    u, x, t, _ = _setup(pkg, seed=7)
+    try:
+        losses = [pkg.binding.transec_unet_train_step(u, x, t, 1e-3)[0] for _ in range(60)]
+        assert losses[-1] < 0.5 * losses[0], losses[::10]
+    finally:
+        pkg.binding.transec_unet_destroy(u)
