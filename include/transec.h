@@ -286,7 +286,45 @@ int transec_unet_forward(transec_unet* u, const float* in, float* out, int on_de
  * layout) may be NULL.  Device or host arrays. */
 int transec_unet_train_step(transec_unet* u, const float* in, const float* target, float lr,
                             float* loss, float* grads, int on_device);
+/* Volume the network was built for.  Any output may be NULL. */
+int transec_unet_dims(const transec_unet* u, int* nx, int* ny, int* nz);
 const char* transec_unet_last_error(const transec_unet* u);
+
+/*
+ * Fit the network to the operator family of `ctx` (same volume): `steps` Adam steps
+ * at learning rate lr, each on one pair (r, e) with r = A(E, k) e, E uniform in
+ * [e_lo, e_hi] and k uniform over the mesh, all drawn from `seed`.  source 0: e is a
+ * seeded random complex field (standard normals smoothed by 0, 1, 2, 3, 5 or 8 passes
+ * of a [1 2 1]/4 filter per axis; periodic in x and y, zero outside in z).  source 1:
+ * e = x* - x_i for up to 48 iterates x_i (x_0 = 0 included) of a transpose-BiCG solve
+ * of a random left-CAP column at opts.tol / opts.maxit, x* its solution; the pairs of
+ * one column are used once each, in random order, before the next column is drawn.
+ * The network input is (s_r Re r, s_r Im r, V - E, Gamma) and the target s_e e, with
+ * s_r = sqrt(n) / ||r|| and s_e = sqrt(n) / ||e||.  loss_out (host, `steps` floats,
+ * may be NULL) receives each step's relative loss.  Errors: EINVAL (arguments, volume
+ * mismatch), ESTATE, ENOMEM, ECUDA; ENOCONV / EBREAKDOWN when the column solves of
+ * source 1 keep failing.
+ */
+int transec_unet_train_operator(transec_ctx* ctx, transec_unet* net, int source, int steps,
+                                double e_lo, double e_hi, float lr, unsigned long long seed,
+                                float* loss_out);
+
+/*
+ * Sampled columns by FGMRES(restart) with the network as right preconditioner on every
+ * net_every-th Arnoldi step (1: every step; 2: alternating with the identity) and the
+ * identity on the others; net == NULL gives plain restarted GMRES.  Item i solves
+ * A(energies[i], k_{ik[i]}) x = e_j for the cols[i]-th left-CAP column to
+ * ||e_j - A x|| <= opts.tol in FP64 and writes t_out[i] = t_j.  A column whose residual
+ * has not halved over 10 restart cycles, that reaches maxit operator applications, or
+ * whose Hessenberg matrix turns singular (a zero preconditioned direction) is solved
+ * again by the plain FP64 Krylov engine (fallback_out[i] = 1).  iters_out
+ * receives the operator applications of both.  Host arrays; returns the most severe
+ * item status (failed items get t = NaN).  Errors: EINVAL, ESTATE, ENOMEM, ECUDA.
+ */
+int transec_fgmres_columns(transec_ctx* ctx, transec_unet* net, int net_every, int nitems,
+                           const double* energies, const int* ik, const int64_t* cols,
+                           int restart, int maxit, double* t_out, int* iters_out,
+                           int* status_out, int* fallback_out);
 void transec_unet_destroy(transec_unet* u);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next

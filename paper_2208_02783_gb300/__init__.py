@@ -17,7 +17,9 @@ from .binding import (  # noqa: F401
     transec_get_solver, transec_last_error, transec_n_rhs, transec_set_abc,
     transec_set_kmesh, transec_set_potential, transec_set_solver, transec_stats,
     transec_stats_reset, transec_status_string, transec_trace, transec_transmission,
-    transec_version,
+    transec_version, transec_fgmres_columns, transec_unet_create, transec_unet_destroy,
+    transec_unet_dims, transec_unet_forward, transec_unet_get_params, transec_unet_n_params,
+    transec_unet_set_params, transec_unet_train_operator, transec_unet_train_step,
 )
 
 
@@ -146,6 +148,50 @@ class Transec:
 
     def __exit__(self, *exc):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LearnedPreconditioner:
+    """The U-Net right preconditioner for one ``Transec`` context's volume: fitted to
+    that operator family on the GPU, then used by FGMRES(restart) for sampled columns."""
+
+    def __init__(self, transec: Transec, seed=0, device=0):
+        nz, ny, nx = transec.shape
+        self.transec = transec
+        self.net = transec_unet_create(device, nx, ny, nz, seed)
+        # the output layer starts at zero weights: the first steps then learn a correlation
+        # with the target instead of shrinking a random output of the wrong scale
+        p = transec_unet_get_params(self.net)
+        w_out = 27 * 2 * 16
+        p[-(w_out + 2):-2] = 0.0
+        transec_unet_set_params(self.net, p)
+
+    def train(self, steps, e_lo, e_hi, lr=1e-3, seed=0, source="krylov"):
+        """Adam steps on pairs (r = A e, e) from Krylov iterates ("krylov") or random
+        fields ("random"); returns the per-step relative losses."""
+        src = {"random": 0, "krylov": 1}[source]
+        return transec_unet_train_operator(self.transec.ctx, self.net, steps, e_lo, e_hi, lr, seed, src)
+
+    def params(self):
+        return transec_unet_get_params(self.net)
+
+    def set_params(self, p):
+        transec_unet_set_params(self.net, p)
+
+    def fgmres_columns(self, energies, ik, cols, restart=30, maxit=20000, precondition=True, net_every=2):
+        t, it, st, fb = transec_fgmres_columns(self.transec.ctx, self.net if precondition else None,
+                                               energies, ik, cols, restart, maxit, net_every)
+        return {"t": t, "iters": it, "status": st, "fallback": fb}
+
+    def close(self):
+        if self.net:
+            transec_unet_destroy(self.net)
+            self.net = None
 
     def __del__(self):
         try:

@@ -89,7 +89,12 @@ _SIGS = {
     "transec_unet_get_params": (C.c_int, [_P, _P]),
     "transec_unet_forward": (C.c_int, [_P, _P, _P, C.c_int]),
     "transec_unet_train_step": (C.c_int, [_P, _P, _P, C.c_float, C.POINTER(C.c_float), _P, C.c_int]),
+    "transec_unet_dims": (C.c_int, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "transec_unet_last_error": (C.c_char_p, [_P]),
+    "transec_unet_train_operator": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_double, C.c_double, C.c_float,
+                                             C.c_ulonglong, _P]),
+    "transec_fgmres_columns": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P,
+                                         _P]),
     "transec_unet_destroy": (None, [_P]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
@@ -425,3 +430,39 @@ def transec_unet_train_step(u, x, target, lr, want_grads=False):
 def transec_unet_destroy(u):
     if u:
         load().transec_unet_destroy(u)
+
+
+def transec_unet_dims(u):
+    d = [C.c_int(), C.c_int(), C.c_int()]
+    _ucheck(u, load().transec_unet_dims(u, *[C.byref(x) for x in d]), "transec_unet_dims")
+    return tuple(x.value for x in d)
+
+
+def transec_unet_train_operator(ctx, u, steps, e_lo, e_hi, lr, seed=0, source=1):
+    """Fit the network to the context's operator family; returns the per-step losses."""
+    loss = np.zeros(max(int(steps), 1), np.float32)
+    st = load().transec_unet_train_operator(ctx, u, int(source), int(steps), float(e_lo), float(e_hi), float(lr),
+                                            int(seed), loss.ctypes.data_as(C.c_void_p))
+    _check(ctx, st, "transec_unet_train_operator")
+    return loss[: int(steps)]
+
+
+def transec_fgmres_columns(ctx, u, energies, ik, cols, restart=30, maxit=20000, net_every=2):
+    """FGMRES(restart) columns with the network (None: unpreconditioned) as right
+    preconditioner on every net_every-th step; returns (t, iters, status, fallback)."""
+    e = np.ascontiguousarray(energies, np.float64)
+    k = np.ascontiguousarray(ik, np.int32)
+    c = np.ascontiguousarray(cols, np.int64)
+    n = e.size
+    if k.size != n or c.size != n:
+        raise ValueError("energies, ik and cols differ in length")
+    t = np.zeros(n, np.float64)
+    it = np.zeros(n, np.int32)
+    so = np.zeros(n, np.int32)
+    fb = np.zeros(n, np.int32)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    st = load().transec_fgmres_columns(ctx, u if u else None, int(net_every), n, vp(e), vp(k), vp(c),
+                                       int(restart), int(maxit),
+                                       vp(t), vp(it), vp(so), vp(fb))
+    _check(ctx, st, "transec_fgmres_columns", allow=(ENOCONV, EBREAKDOWN))
+    return t, it, so, fb

@@ -393,6 +393,14 @@ int transec_unet_train_step(transec_unet* u, const float* in, const float* targe
   return rc;
 }
 
+int transec_unet_dims(const transec_unet* u, int* nx, int* ny, int* nz) {
+  if (!u) return TRANSEC_EINVAL;
+  if (nx) *nx = u->nx;
+  if (ny) *ny = u->ny;
+  if (nz) *nz = u->nz;
+  return TRANSEC_OK;
+}
+
 const char* transec_unet_last_error(const transec_unet* u) { return u ? u->err.c_str() : ""; }
 
 void transec_unet_destroy(transec_unet* u) {

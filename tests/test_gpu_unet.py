@@ -2,8 +2,13 @@
 
 The GPU runs BF16 tensor-core convolutions with FP32 accumulation, so values and
 gradients are compared by relative L2 error, with bars that BF16 storage of the
-activations (8 significant bits) and of the gradients fixes: 3e-2 for the output, 6e-2
-for each parameter gradient.  The reference itself is pinned by finite differences in
+activations (8 significant bits) and of the gradients fixes.  Rounding the reference's
+activations, weights and back-propagated gradients to BF16 at the points where the GPU
+stores them (and nothing else) moves its output by 0.3-0.6% and its parameter
+gradients by up to 5% (up to 7.2% for the first layer's weights, whose gradient passes
+through every rounding of the backward chain) on these shapes and seeds.  The bars are
+about twice that: 3e-2 for the output, 0.10 for each parameter gradient, 0.15 for the
+first layer's weights.  The reference itself is pinned by finite differences in
 tests/test_oracle_unet.py.
 """
 
@@ -79,7 +84,8 @@ def test_gradients_match_reference():
         gg = _unflatten(g)
         for name, *_ in ref.LAYERS:
             for suffix in (".w", ".b"):
-                assert _rel(gg[name + suffix], gr[name + suffix]) <= 6e-2, name + suffix
+                bar = 0.15 if name + suffix == "e1a.w" else 0.10
+                assert _rel(gg[name + suffix], gr[name + suffix]) <= bar, name + suffix
     finally:
         pkg.binding.transec_unet_destroy(u)
 
