@@ -273,6 +273,119 @@ def run_uneven_batch(args):
     return 0
 
 
+UNET_LAYERS = [(4, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 64, 2),
+               (96, 32, 1), (32, 32, 1), (48, 16, 0), (16, 16, 0), (16, 2, 0)]  # (cin, cout, level)
+
+
+def unet_forward_flops(nvox: int, padded: bool) -> float:
+    """Multiply-add flops of one U-Net forward: 2 x 27 x cin x cout per voxel of each
+    convolution's level (level l has nvox / 8^l voxels); padded=True counts the channels
+    rounded up to 16 as the tensor cores execute them."""
+    pad = (lambda c: (c + 15) // 16 * 16) if padded else (lambda c: c)
+    return float(sum(2 * 27 * pad(ci) * pad(co) * nvox / 8 ** lv for ci, co, lv in UNET_LAYERS))
+
+
+def run_learned(args):
+    """Learned right preconditioner (growth form): the U-Net forward on the bulk Cu
+    volume (20x20x480, the network's per-Arnoldi-step cost), timed with CUDA events, and
+    the FGMRES(30) gain on a 16x16x32 order-4 cell (operator applications and time per
+    column with the network on alternate steps, without it, and with the plain FP64
+    engine)."""
+    import torch
+
+    from workloads import cu_bulk, small_instance
+    import paper_2208_02783_gb300 as pkg
+    from paper_2208_02783_gb300 import build
+
+    pkg.load(build.build())
+    inst = cu_bulk()
+    tr = pkg.Transec.from_instance(inst, device=0)
+    lp = pkg.LearnedPreconditioner(tr, seed=1)
+    n = tr.n
+    x = torch.randn(n, 4, device="cuda", dtype=torch.float32)
+    y = torch.empty(n, 2, device="cuda", dtype=torch.float32)
+    for _ in range(max(3, args.warmup)):
+        pkg.transec_unet_forward(lp.net, x, y)
+    torch.cuda.synchronize()
+    steps = max(10, args.steps)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(0)
+    clocks.start()
+    ev0.record()
+    for _ in range(steps):
+        pkg.transec_unet_forward(lp.net, x, y)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / steps
+    # end to end: host input in, host output out
+    xh = x.cpu().pin_memory()
+    yh = torch.empty(n, 2, dtype=torch.float32).pin_memory()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        pkg.transec_unet_forward(lp.net, xh, yh)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+    lp.close()
+    tr.close()
+    fl_alg = unet_forward_flops(n, False)
+    fl_pad = unet_forward_flops(n, True)
+    peaks = measured_peaks()
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    achieved = fl_alg / (ms / 1e3) / 1e12
+
+    # FGMRES gain on the small cell
+    cell = small_instance(16, 16, 32, 0.4, 4, 8, energies=(0.3,), seed=3)
+    cols = np.array([0, 37, 100, 511, 1500])
+    e = np.full(cols.size, 0.3)
+    ik = np.zeros(cols.size, np.int32)
+    gain = {}
+    with pkg.Transec.from_instance(cell) as tc:
+        t0 = time.perf_counter()
+        plain = tc.column_contributions(e, ik, cols)
+        gain["plain_engine"] = {"applies_per_column": float(plain["iters"].mean()),
+                                "ms_per_column": (time.perf_counter() - t0) * 1e3 / cols.size}
+        lpc = pkg.LearnedPreconditioner(tc, seed=1)
+        t0 = time.perf_counter()
+        g0 = lpc.fgmres_columns(e, ik, cols, precondition=False, maxit=6000)
+        gain["gmres30"] = {"applies_per_column": float(g0["iters"].mean()),
+                           "ms_per_column": (time.perf_counter() - t0) * 1e3 / cols.size,
+                           "fallbacks": int(g0["fallback"].sum())}
+        t0 = time.perf_counter()
+        loss = lpc.train(1500, 0.2, 0.4, lr=1e-3, seed=5, source="krylov")
+        gain["training"] = {"steps": 1500, "s": time.perf_counter() - t0,
+                            "loss_first100": float(loss[:100].mean()), "loss_last100": float(loss[-100:].mean())}
+        t0 = time.perf_counter()
+        g1 = lpc.fgmres_columns(e, ik, cols, maxit=6000, net_every=2)
+        gain["fgmres30_net_alternate"] = {"applies_per_column": float(g1["iters"].mean()),
+                                          "ms_per_column": (time.perf_counter() - t0) * 1e3 / cols.size,
+                                          "fallbacks": int(g1["fallback"].sum()),
+                                          "max_abs_dt_vs_plain": float(np.abs(g1["t"] - plain["t"]).max())}
+        lpc.close()
+    line = {
+        "metric": "learned preconditioner: U-Net forward voxels/s on the bulk Cu volume",
+        "value": n / (ms / 1e3), "unit": "voxels/s", "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup),
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "U-Net 16/32/64 on 20x20x480 (bulk fcc Cu [001] volume), FP32 input/output, "
+                               "BF16 activations and weights, FP32 accumulation",
+                   "fgmres_gain_16x16x32_order4": gain,
+                   "l2": "activations ~60 MB per forward fit in L2; no flush (the preconditioner re-reads "
+                         "its weights every Arnoldi step)"},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "whole forward (11 k_conv launches + pool/upsample/concat)",
+                     "flops_algorithmic": fl_alg, "flops_padded_channels": fl_pad,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured cuBLAS burst)"},
+        "e2e": {"value": n / (e2e_ms / 1e3), "unit": "voxels/s", "h2d_bytes_per_step": n * 16,
+                "d2h_bytes_per_step": n * 8},
+        "gpu_launches": 18 * steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -285,13 +398,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="small bounded run for ncu: 32 columns, 40 iterations each, then exit")
-    ap.add_argument("--workload", default="cu_bulk", choices=["cu_bulk", "uneven_batch"],
-                    help="uneven_batch: the 96-cell mixed batch, batched vs looped per cell")
+    ap.add_argument("--workload", default="cu_bulk", choices=["cu_bulk", "uneven_batch", "learned"],
+                    help="uneven_batch: the 96-cell mixed batch, batched vs looped per cell; "
+                         "learned: the U-Net preconditioner's forward and FGMRES gain")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "uneven_batch":
         return run_uneven_batch(args)
+    if args.workload == "learned":
+        return run_learned(args)
 
     import torch
     import torch.distributed as dist

@@ -2,6 +2,7 @@
 // backward, Adam, and the C ABI (transec_unet_*).  See unet.cuh for the kernels.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <random>
@@ -51,6 +52,9 @@ struct transec_unet {
   float* out = nullptr;  // [n0][16]
   bf16 *gA = nullptr, *gB = nullptr, *gC = nullptr, *gSkip1 = nullptr, *gSkip2 = nullptr;
   double* sums = nullptr;
+  double* lpart = nullptr;  // per-block loss partial sums [256][2]
+  float* wpart = nullptr;   // per-chunk weight-gradient partial sums
+  float* bpart = nullptr;   // per-block bias-gradient partial sums
   float* in_buf = nullptr;
   cudaStream_t s = nullptr;
   std::string err;
@@ -98,25 +102,34 @@ void conv(transec_unet* u, int l, const bf16* x, bf16* y, float* yf, long long n
     a.cin = L.cout_p; a.cout = L.cin_p; a.relu = 0;
   }
   a.nx = nx; a.ny = ny; a.nz = nz; a.nvox = nvox;
-  const unsigned grid = (unsigned)((nvox + 63) / 64);
-  switch (a.cout / 8) {
-    case 2: k_conv<2><<<grid, 128, 0, u->s>>>(a); break;
-    case 4: k_conv<4><<<grid, 128, 0, u->s>>>(a); break;
-    case 6: k_conv<6><<<grid, 128, 0, u->s>>>(a); break;
-    case 8: k_conv<8><<<grid, 128, 0, u->s>>>(a); break;
-    case 12: k_conv<12><<<grid, 128, 0, u->s>>>(a); break;
-    default: break;
+  const size_t smem = conv_smem_bytes(a.cin);
+  const unsigned groups = (unsigned)(a.cout / 16);
+  // two m-tiles per warp where that still leaves 8 blocks per SM on 152 SMs
+  if ((nvox + 127) / 128 * groups >= 152 * 8) {
+    k_conv<2><<<dim3((unsigned)((nvox + 127) / 128), groups), 128, smem, u->s>>>(a);
+  } else {
+    k_conv<1><<<dim3((unsigned)((nvox + 63) / 64), groups), 128, smem, u->s>>>(a);
   }
 }
+
+int wgrad_chunk(long long nvox) {
+  const long long c = (nvox + 1023) / 1024;
+  return (int)std::max<long long>(512, (c + 15) / 16 * 16);
+}
+
+const int kBiasBlocks = 120;
 
 void wgrad(transec_unet* u, int l, const bf16* x, const bf16* dy, long long nvox, int nx, int ny, int nz) {
   const Layer& L = u->L[l];
   WgradArgs a{};
-  a.x = x; a.dy = dy; a.dw = u->g + L.w_off; a.cin = L.cin_p; a.cout = L.cout_p;
-  a.nx = nx; a.ny = ny; a.nz = nz; a.nvox = nvox; a.chunk = 512;
-  k_wgrad<<<dim3(27, (unsigned)((nvox + a.chunk - 1) / a.chunk)), 128, 0, u->s>>>(a);
-  k_bias_grad<<<std::min<unsigned>(grid_for(nvox * L.cout_p), 2048u), 256, 0, u->s>>>(dy, u->g + L.b_off,
-                                                                                     L.cout_p, nvox);
+  a.x = x; a.dy = dy; a.part = u->wpart; a.cin = L.cin_p; a.cout = L.cout_p;
+  a.nx = nx; a.ny = ny; a.nz = nz; a.nvox = nvox; a.chunk = wgrad_chunk(nvox);
+  const unsigned nchunks = (unsigned)((nvox + a.chunk - 1) / a.chunk);
+  const long long nw = 27LL * L.cout_p * L.cin_p;
+  k_wgrad<<<dim3(27, nchunks), 128, 0, u->s>>>(a);
+  k_wgrad_reduce<<<grid_for(nw), 256, 0, u->s>>>(u->wpart, u->g + L.w_off, nw, (int)nchunks);
+  k_bias_grad<<<kBiasBlocks, 256, 0, u->s>>>(dy, u->bpart, L.cout_p, nvox);
+  k_bias_reduce<<<1, 128, 0, u->s>>>(u->bpart, u->g + L.b_off, L.cout_p, kBiasBlocks);
 }
 
 __global__ void k_to_bf16(const float* p, bf16* q, long long n) {
@@ -237,7 +250,28 @@ int transec_unet_create(transec_unet** out, int device, int nx, int ny, int nz, 
   bf(&u->gSkip1, u->n0 * 16); bf(&u->gSkip2, u->n1 * 32);
   fl(&u->in_buf, u->n0 * 4);
   if (rc == TRANSEC_OK && cudaMalloc(&u->sums, 2 * sizeof(double)) != cudaSuccess) rc = TRANSEC_ENOMEM;
+  if (rc == TRANSEC_OK && cudaMalloc(&u->lpart, 512 * sizeof(double)) != cudaSuccess) rc = TRANSEC_ENOMEM;
+  {
+    // the largest [chunks][27][cout][cin] slice set over the layers (level of each layer
+    // from the execution order: e1*, d1*, out at full size; e2*, d2* at 1/8; e3* at 1/64)
+    const int level[kL] = {0, 0, 1, 1, 2, 2, 1, 1, 0, 0, 0};
+    long long wp = 0;
+    for (int l = 0; l < kL; ++l) {
+      const long long nv = level[l] == 0 ? u->n0 : level[l] == 1 ? u->n1 : u->n2;
+      const long long ch = (nv + wgrad_chunk(nv) - 1) / wgrad_chunk(nv);
+      wp = std::max(wp, ch * 27LL * u->L[l].cout_p * u->L[l].cin_p);
+    }
+    fl(&u->wpart, wp);
+    fl(&u->bpart, (long long)kBiasBlocks * 96);
+  }
   if (rc == TRANSEC_OK && cudaStreamCreateWithFlags(&u->s, cudaStreamNonBlocking) != cudaSuccess) rc = TRANSEC_ECUDA;
+  // the widest convolution input has 96 channels
+  if (rc == TRANSEC_OK &&
+      (cudaFuncSetAttribute(k_conv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem_bytes(96)) !=
+           cudaSuccess ||
+       cudaFuncSetAttribute(k_conv<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem_bytes(96)) !=
+           cudaSuccess))
+    rc = TRANSEC_ECUDA;
   if (rc != TRANSEC_OK) {
     cudaGetLastError();
     transec_unet_destroy(u);
@@ -364,8 +398,8 @@ int transec_unet_train_step(transec_unet* u, const float* in, const float* targe
   k_input<<<grid_for(u->n0 * 16), 256, 0, u->s>>>(din, u->x0, u->n0);
   int rc = forward(u);
   if (rc == TRANSEC_OK) {
-    cudaMemsetAsync(u->sums, 0, 2 * sizeof(double), u->s);
-    k_loss_sums<<<256, 256, 0, u->s>>>(u->out, dt, u->n0, u->sums);
+    k_loss_sums<<<256, 256, 0, u->s>>>(u->out, dt, u->n0, u->lpart);
+    k_loss_final<<<1, 32, 0, u->s>>>(u->lpart, 256, u->sums);
     k_loss_grad<<<grid_for(u->n0 * 16), 256, 0, u->s>>>(u->out, dt, u->sums, u->gA, u->n0);
     rc = backward(u);
   }
@@ -412,7 +446,7 @@ void transec_unet_destroy(transec_unet* u) {
                   (void*)u->p2, (void*)u->e3a, (void*)u->a3, (void*)u->u3, (void*)u->cat2, (void*)u->d2a,
                   (void*)u->d2, (void*)u->u2, (void*)u->cat1, (void*)u->d1a, (void*)u->d1, (void*)u->out,
                   (void*)u->gA, (void*)u->gB, (void*)u->gC, (void*)u->gSkip1, (void*)u->gSkip2,
-                  (void*)u->sums, (void*)u->in_buf})
+                  (void*)u->sums, (void*)u->lpart, (void*)u->wpart, (void*)u->bpart, (void*)u->in_buf})
     if (q) cudaFree(q);
   if (u->s) cudaStreamDestroy(u->s);
   cudaGetLastError();

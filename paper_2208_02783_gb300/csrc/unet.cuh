@@ -9,7 +9,8 @@
 //                            input channels; the data gradient is the same product
 //                            with transposed, tap-flipped weights;
 //   weight gradient:         rows = output channels, columns = input channels,
-//                            K = voxels of a chunk, one tap per block, FP32 atomics.
+//                            K = voxels of a chunk, one tap per block; per-chunk
+//                            partial sums added in chunk order (deterministic).
 // Weights are [27][Cout][Cin] (tap t = (dz+1)*9 + (dy+1)*3 + (dx+1)); zero outside the
 // volume.
 #pragma once
@@ -61,62 +62,112 @@ struct ConvArgs {
   long long nvox;
 };
 
-// 4 warps x 16 voxels per block; NT = cout / 8 column tiles per warp.
-template <int NT>
+// Forward / data-gradient convolution.  Block = 4 warps; blockIdx.y picks a group of 16
+// output channels, whose weights for all 27 taps are staged once in shared memory
+// ([27][16][cin + 8]: the 16-byte row pad makes the B-fragment reads bank-conflict
+// free); each warp computes MT m-tiles of 16 voxels x 16 channels, so one B fragment
+// feeds MT tensor-core products.  Dynamic shared memory: conv_smem_bytes(cin).
+__host__ __device__ constexpr int conv_ldw(int cin) { return cin + 8; }
+__host__ __device__ constexpr size_t conv_smem_bytes(int cin) { return (size_t)27 * 16 * conv_ldw(cin) * 2; }
+
+template <int MT>
 __global__ void __launch_bounds__(128) k_conv(const ConvArgs a) {
+  extern __shared__ __align__(16) unsigned char conv_smem[];
+  bf16* ws = reinterpret_cast<bf16*>(conv_smem);
+  const int ldw = conv_ldw(a.cin);
+  const int co0 = blockIdx.y * 16;
+  const int cpr = a.cin / 8;  // 16-byte chunks per weight row
+  for (int idx = threadIdx.x; idx < 27 * 16 * cpr; idx += blockDim.x) {
+    const int row = idx / cpr, ch = idx - row * cpr;
+    const int tap = row >> 4, o = row & 15;
+    const uint4 v = *reinterpret_cast<const uint4*>(a.w + ((long long)tap * a.cout + co0 + o) * a.cin + ch * 8);
+    *reinterpret_cast<uint4*>(ws + row * ldw + ch * 8) = v;
+  }
+  __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const long long v0 = (long long)blockIdx.x * 64 + warp * 16;
-  const long long r0 = v0 + g, r1 = v0 + g + 8;
-  const long long q0 = r0 < a.nvox ? r0 : -1, q1 = r1 < a.nvox ? r1 : -1;
-  float acc[NT][4];
+  const long long vbase = (long long)blockIdx.x * (64 * MT) + warp * (16 * MT);
+  // coordinates of the 2 x MT rows this thread feeds (-1: past the end)
+  long long row[MT][2];
+  int cx[MT][2], cy[MT][2], cz[MT][2];
 #pragma unroll
-  for (int n = 0; n < NT; ++n)
+  for (int m = 0; m < MT; ++m)
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[n][k] = 0.f;
+    for (int h = 0; h < 2; ++h) {
+      const long long v = vbase + m * 16 + g + 8 * h;
+      row[m][h] = v < a.nvox ? v : -1;
+      const long long vv = v < a.nvox ? v : 0;
+      cx[m][h] = (int)(vv % a.nx);
+      cy[m][h] = (int)((vv / a.nx) % a.ny);
+      cz[m][h] = (int)(vv / ((long long)a.nx * a.ny));
+    }
+  float acc[MT][2][4];
+#pragma unroll
+  for (int m = 0; m < MT; ++m)
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[m][n][k] = 0.f;
   const int kchunks = a.cin / 16;
+  const long long sxy = (long long)a.nx * a.ny;
   for (int tap = 0; tap < 27; ++tap) {
-    const long long n0 = neighbour(q0, tap, a.nx, a.ny, a.nz);
-    const long long n1 = neighbour(q1, tap, a.nx, a.ny, a.nz);
-    const bf16* x0 = a.x + (n0 >= 0 ? n0 : 0) * a.cin;
-    const bf16* x1 = a.x + (n1 >= 0 ? n1 : 0) * a.cin;
-    const bf16* wt = a.w + (long long)tap * a.cout * a.cin;
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const long long off = dx + (long long)a.nx * dy + sxy * dz;
+    const bf16* xp[MT][2];
+    bool ok[MT][2];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int xx = cx[m][h] + dx, yy = cy[m][h] + dy, zz = cz[m][h] + dz;
+        ok[m][h] = row[m][h] >= 0 && xx >= 0 && xx < a.nx && yy >= 0 && yy < a.ny && zz >= 0 && zz < a.nz;
+        xp[m][h] = a.x + (ok[m][h] ? (row[m][h] + off) * a.cin : 0);
+      }
+    const bf16* wt = ws + tap * 16 * ldw;
     for (int kc = 0; kc < kchunks; ++kc) {
       const int k0 = kc * 16 + 2 * t;
-      const uint32_t a0 = n0 >= 0 ? ld_pair(x0 + k0) : 0u;
-      const uint32_t a1 = n1 >= 0 ? ld_pair(x1 + k0) : 0u;
-      const uint32_t a2 = n0 >= 0 ? ld_pair(x0 + k0 + 8) : 0u;
-      const uint32_t a3 = n1 >= 0 ? ld_pair(x1 + k0 + 8) : 0u;
+      uint32_t b[2][2];
 #pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        const bf16* wr = wt + (long long)(n * 8 + g) * a.cin + k0;
-        mma_bf16(acc[n], a0, a1, a2, a3, ld_pair(wr), ld_pair(wr + 8));
+      for (int n = 0; n < 2; ++n) {
+        const bf16* wr = wt + (n * 8 + g) * ldw + k0;
+        b[n][0] = ld_pair(wr);
+        b[n][1] = ld_pair(wr + 8);
+      }
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        const uint32_t a0 = ok[m][0] ? ld_pair(xp[m][0] + k0) : 0u;
+        const uint32_t a1 = ok[m][1] ? ld_pair(xp[m][1] + k0) : 0u;
+        const uint32_t a2 = ok[m][0] ? ld_pair(xp[m][0] + k0 + 8) : 0u;
+        const uint32_t a3 = ok[m][1] ? ld_pair(xp[m][1] + k0 + 8) : 0u;
+#pragma unroll
+        for (int n = 0; n < 2; ++n) mma_bf16(acc[m][n], a0, a1, a2, a3, b[n][0], b[n][1]);
       }
     }
   }
 #pragma unroll
-  for (int n = 0; n < NT; ++n) {
-    const int c = n * 8 + 2 * t;
-    const float b0 = a.b ? a.b[c] : 0.f, b1 = a.b ? a.b[c + 1] : 0.f;
-    float v[4] = {acc[n][0] + b0, acc[n][1] + b1, acc[n][2] + b0, acc[n][3] + b1};
-    if (a.relu)
+  for (int m = 0; m < MT; ++m)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) v[k] = fmaxf(v[k], 0.f);
-    if (r0 < a.nvox) {
-      if (a.y) *reinterpret_cast<__nv_bfloat162*>(a.y + r0 * a.cout + c) = __floats2bfloat162_rn(v[0], v[1]);
-      if (a.yf) { a.yf[r0 * a.cout + c] = v[0]; a.yf[r0 * a.cout + c + 1] = v[1]; }
+    for (int n = 0; n < 2; ++n) {
+      const int c = co0 + n * 8 + 2 * t;
+      const float b0 = a.b ? a.b[c] : 0.f, b1 = a.b ? a.b[c + 1] : 0.f;
+      float v[4] = {acc[m][n][0] + b0, acc[m][n][1] + b1, acc[m][n][2] + b0, acc[m][n][3] + b1};
+      if (a.relu)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = fmaxf(v[k], 0.f);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long r = row[m][h];
+        if (r < 0) continue;
+        if (a.y) *reinterpret_cast<__nv_bfloat162*>(a.y + r * a.cout + c) = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+        if (a.yf) { a.yf[r * a.cout + c] = v[2 * h]; a.yf[r * a.cout + c + 1] = v[2 * h + 1]; }
+      }
     }
-    if (r1 < a.nvox) {
-      if (a.y) *reinterpret_cast<__nv_bfloat162*>(a.y + r1 * a.cout + c) = __floats2bfloat162_rn(v[2], v[3]);
-      if (a.yf) { a.yf[r1 * a.cout + c] = v[2]; a.yf[r1 * a.cout + c + 1] = v[3]; }
-    }
-  }
 }
 
 struct WgradArgs {
   const bf16* x;   // [nvox][cin]  layer input
   const bf16* dy;  // [nvox][cout] gradient of the layer output (after the ReLU mask)
-  float* dw;       // [27][cout][cin] accumulated with atomics
+  float* part;     // [chunks][27][cout][cin] per-block partial sums
   int cin, cout, nx, ny, nz, chunk;
   long long nvox;
 };
@@ -163,18 +214,28 @@ __global__ void __launch_bounds__(128) k_wgrad(const WgradArgs a) {
         if (jj == j) mma_bf16(acc[jj], a0, a1, a2, a3, b0, b1);
     }
   }
+  // this block's partial sums go to its own slice; k_wgrad_reduce adds the slices in order
   int j = 0;
   for (int nt = nfirst; nt < NTT; nt += nstride, ++j) {
     const int co0 = mt * 16 + g, ci0 = nt * 8 + 2 * t;
-    float* base = a.dw + (long long)tap * a.cout * a.cin;
+    float* base = a.part + ((long long)blockIdx.y * 27 + tap) * a.cout * a.cin;
 #pragma unroll
     for (int jj = 0; jj < 12; ++jj) {
       if (jj != j) continue;
-      atomicAdd(base + (long long)co0 * a.cin + ci0, acc[jj][0]);
-      atomicAdd(base + (long long)co0 * a.cin + ci0 + 1, acc[jj][1]);
-      atomicAdd(base + (long long)(co0 + 8) * a.cin + ci0, acc[jj][2]);
-      atomicAdd(base + (long long)(co0 + 8) * a.cin + ci0 + 1, acc[jj][3]);
+      base[(long long)co0 * a.cin + ci0] = acc[jj][0];
+      base[(long long)co0 * a.cin + ci0 + 1] = acc[jj][1];
+      base[(long long)(co0 + 8) * a.cin + ci0] = acc[jj][2];
+      base[(long long)(co0 + 8) * a.cin + ci0 + 1] = acc[jj][3];
     }
+  }
+}
+
+// dw[e] = sum over the chunks, in chunk order, of part[chunk][e] (e < 27 cout cin)
+static __global__ void k_wgrad_reduce(const float* part, float* dw, long long nw, int nchunks) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nw; e += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int c = 0; c < nchunks; ++c) s += part[(long long)c * nw + e];
+    dw[e] = s;
   }
 }
 
@@ -277,13 +338,34 @@ static __global__ void k_relu_bwd(bf16* dy, const bf16* y, long long n) {
 }
 
 // bias gradient db[c] += sum_v dy[v][c]
-static __global__ void k_bias_grad(const bf16* dy, float* db, int C, long long nvox) {
-  __shared__ float s[64];
-  for (int c = threadIdx.x; c < C; c += blockDim.x) s[c] = 0.f;
+// per-block partial bias gradients part[block][c] = sum over the block's voxel range of
+// dy[v][c]: thread (r, c) with r = tid / C sums voxels r, r + R, ... (R = blockDim / C),
+// then the R sums are added in order.  C <= 96, blockDim = 256.
+static __global__ void k_bias_grad(const bf16* dy, float* part, int C, long long nvox) {
+  __shared__ float s[256];
+  const int R = blockDim.x / C;
+  const int r = threadIdx.x / C, c = threadIdx.x % C;
+  const long long per = (nvox + gridDim.x - 1) / gridDim.x;
+  const long long v0 = (long long)blockIdx.x * per, v1 = v0 + per < nvox ? v0 + per : nvox;
+  float acc = 0.f;
+  if (r < R)
+    for (long long v = v0 + r; v < v1; v += R) acc += __bfloat162float(dy[v * C + c]);
+  s[threadIdx.x] = acc;
   __syncthreads();
-  GRID_STRIDE(i, nvox * C) atomicAdd(&s[i % C], __bfloat162float(dy[i]));
-  __syncthreads();
-  for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&db[c], s[c]);
+  if (threadIdx.x < C) {
+    float tot = 0.f;
+    for (int q = 0; q < R; ++q) tot += s[q * C + threadIdx.x];
+    part[(long long)blockIdx.x * C + threadIdx.x] = tot;
+  }
+}
+
+// db[c] = sum over blocks, in order, of part[block][c]
+static __global__ void k_bias_reduce(const float* part, float* db, int C, int nblk) {
+  const int c = threadIdx.x;
+  if (c >= C) return;
+  float s = 0.f;
+  for (int b = 0; b < nblk; ++b) s += part[(long long)b * C + c];
+  db[c] = s;
 }
 
 // transposed, tap-flipped weights for the data gradient: wt[26-t][i][o] = w[t][o][i]
@@ -306,7 +388,9 @@ static __global__ void k_input(const float* in, bf16* x, long long nvox) {
 
 // relative loss sums: s[0] += sum |y - t|^2, s[1] += sum |t|^2 (y: [nvox][16] FP32,
 // channels 0, 1 used; t: [nvox][2])
-static __global__ void k_loss_sums(const float* y, const float* t, long long nvox, double* s) {
+// per-block partial sums part[block] = (sum |y - t|^2, sum |t|^2) over channels 0, 1;
+// blockDim = 256
+static __global__ void k_loss_sums(const float* y, const float* t, long long nvox, double* part) {
   double a = 0.0, b = 0.0;
   GRID_STRIDE(v, nvox) {
     for (int c = 0; c < 2; ++c) {
@@ -315,14 +399,31 @@ static __global__ void k_loss_sums(const float* y, const float* t, long long nvo
       b += (double)t[v * 2 + c] * t[v * 2 + c];
     }
   }
+  __shared__ double red[2][8];
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
     b += __shfl_down_sync(0xffffffffu, b, o);
   }
   if ((threadIdx.x & 31) == 0) {
-    atomicAdd(&s[0], a);
-    atomicAdd(&s[1], b);
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < 8; ++w) { sa += red[0][w]; sb += red[1][w]; }
+    part[2 * blockIdx.x] = sa;
+    part[2 * blockIdx.x + 1] = sb;
+  }
+}
+
+// s = sum over blocks, in order, of the partial sums
+static __global__ void k_loss_final(const double* part, int nblk, double* s) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0, b = 0.0;
+  for (int q = 0; q < nblk; ++q) { a += part[2 * q]; b += part[2 * q + 1]; }
+  s[0] = a;
+  s[1] = b;
 }
 
 // dL/dy = 2 (y - t) / sum |t|^2 on channels 0, 1 (zero elsewhere), BF16
