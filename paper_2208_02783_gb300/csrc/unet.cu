@@ -103,13 +103,8 @@ void conv(transec_unet* u, int l, const bf16* x, bf16* y, float* yf, long long n
   }
   a.nx = nx; a.ny = ny; a.nz = nz; a.nvox = nvox;
   const size_t smem = conv_smem_bytes(a.cin);
-  const unsigned groups = (unsigned)(a.cout / 16);
-  // two m-tiles per warp where that still leaves 8 blocks per SM on 152 SMs
-  if ((nvox + 127) / 128 * groups >= 152 * 8) {
-    k_conv<2><<<dim3((unsigned)((nvox + 127) / 128), groups), 128, smem, u->s>>>(a);
-  } else {
-    k_conv<1><<<dim3((unsigned)((nvox + 63) / 64), groups), 128, smem, u->s>>>(a);
-  }
+  const unsigned bricks = (unsigned)(((nx + kBX - 1) / kBX) * ((ny + kBY - 1) / kBY) * ((nz + kBZ - 1) / kBZ));
+  k_conv<<<dim3(bricks, (unsigned)(a.cout / 16)), 128, smem, u->s>>>(a);
 }
 
 int wgrad_chunk(long long nvox) {
@@ -267,10 +262,8 @@ int transec_unet_create(transec_unet** out, int device, int nx, int ny, int nz, 
   if (rc == TRANSEC_OK && cudaStreamCreateWithFlags(&u->s, cudaStreamNonBlocking) != cudaSuccess) rc = TRANSEC_ECUDA;
   // the widest convolution input has 96 channels
   if (rc == TRANSEC_OK &&
-      (cudaFuncSetAttribute(k_conv<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem_bytes(96)) !=
-           cudaSuccess ||
-       cudaFuncSetAttribute(k_conv<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem_bytes(96)) !=
-           cudaSuccess))
+      cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem_bytes(96)) !=
+          cudaSuccess)
     rc = TRANSEC_ECUDA;
   if (rc != TRANSEC_OK) {
     cudaGetLastError();

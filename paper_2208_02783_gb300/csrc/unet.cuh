@@ -62,90 +62,90 @@ struct ConvArgs {
   long long nvox;
 };
 
-// Forward / data-gradient convolution.  Block = 4 warps; blockIdx.y picks a group of 16
-// output channels, whose weights for all 27 taps are staged once in shared memory
-// ([27][16][cin + 8]: the 16-byte row pad makes the B-fragment reads bank-conflict
-// free); each warp computes MT m-tiles of 16 voxels x 16 channels, so one B fragment
-// feeds MT tensor-core products.  Dynamic shared memory: conv_smem_bytes(cin).
+// Forward / data-gradient convolution over bricks of 4 x 4 x 8 voxels (x fastest).
+// Block = 4 warps; blockIdx.x picks the brick, blockIdx.y a group of 16 output
+// channels.  The block stages (a) the group's weights for all 27 taps,
+// [27][16][cin + 8], and (b) the brick's input with a one-voxel halo, [6*6*10][cin + 8]
+// with zeros outside the volume, in shared memory (16-byte row pads).  An m-tile is one
+// z-plane of the brick (16 voxels), so for every tap the A fragment of a thread is a
+// fixed offset from its row in the staged tile: no index arithmetic or bounds checks
+// in the inner loop.  Warp w computes z-planes 2w and 2w + 1 against both 8-channel
+// n-tiles (one B fragment feeds two tensor-core products).  Dynamic shared memory:
+// conv_smem_bytes(cin).
+constexpr int kBX = 4, kBY = 4, kBZ = 8;                   // brick
+constexpr int kHX = kBX + 2, kHY = kBY + 2, kHZ = kBZ + 2;  // with halo
+constexpr int kHV = kHX * kHY * kHZ;
 __host__ __device__ constexpr int conv_ldw(int cin) { return cin + 8; }
-__host__ __device__ constexpr size_t conv_smem_bytes(int cin) { return (size_t)27 * 16 * conv_ldw(cin) * 2; }
+__host__ __device__ constexpr size_t conv_smem_bytes(int cin) {
+  return ((size_t)27 * 16 + kHV) * conv_ldw(cin) * 2;
+}
 
-template <int MT>
 __global__ void __launch_bounds__(128) k_conv(const ConvArgs a) {
   extern __shared__ __align__(16) unsigned char conv_smem[];
+  const int ld = conv_ldw(a.cin);
   bf16* ws = reinterpret_cast<bf16*>(conv_smem);
-  const int ldw = conv_ldw(a.cin);
+  bf16* xs = ws + 27 * 16 * ld;
   const int co0 = blockIdx.y * 16;
-  const int cpr = a.cin / 8;  // 16-byte chunks per weight row
+  const int nbx = (a.nx + kBX - 1) / kBX, nby = (a.ny + kBY - 1) / kBY;
+  const int bx = blockIdx.x % nbx, by = (blockIdx.x / nbx) % nby, bz = blockIdx.x / (nbx * nby);
+  const int x0 = bx * kBX, y0 = by * kBY, z0 = bz * kBZ;
+  const int cpr = a.cin / 8;  // 16-byte chunks per row
   for (int idx = threadIdx.x; idx < 27 * 16 * cpr; idx += blockDim.x) {
     const int row = idx / cpr, ch = idx - row * cpr;
     const int tap = row >> 4, o = row & 15;
     const uint4 v = *reinterpret_cast<const uint4*>(a.w + ((long long)tap * a.cout + co0 + o) * a.cin + ch * 8);
-    *reinterpret_cast<uint4*>(ws + row * ldw + ch * 8) = v;
+    *reinterpret_cast<uint4*>(ws + row * ld + ch * 8) = v;
+  }
+  for (int idx = threadIdx.x; idx < kHV * cpr; idx += blockDim.x) {
+    const int h = idx / cpr, ch = idx - h * cpr;
+    const int gx = x0 - 1 + h % kHX, gy = y0 - 1 + (h / kHX) % kHY, gz = z0 - 1 + h / (kHX * kHY);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
+      v = *reinterpret_cast<const uint4*>(a.x + ((long long)gx + (long long)a.nx * (gy + (long long)a.ny * gz)) * a.cin +
+                                         ch * 8);
+    *reinterpret_cast<uint4*>(xs + h * ld + ch * 8) = v;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
-  const long long vbase = (long long)blockIdx.x * (64 * MT) + warp * (16 * MT);
-  // coordinates of the 2 x MT rows this thread feeds (-1: past the end)
-  long long row[MT][2];
-  int cx[MT][2], cy[MT][2], cz[MT][2];
+  const int lx = g & 3, ly = g >> 2;  // rows g and g + 8 of an m-tile: (lx, ly) and (lx, ly + 2)
+  int base[2][2];
 #pragma unroll
-  for (int m = 0; m < MT; ++m)
+  for (int m = 0; m < 2; ++m)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const long long v = vbase + m * 16 + g + 8 * h;
-      row[m][h] = v < a.nvox ? v : -1;
-      const long long vv = v < a.nvox ? v : 0;
-      cx[m][h] = (int)(vv % a.nx);
-      cy[m][h] = (int)((vv / a.nx) % a.ny);
-      cz[m][h] = (int)(vv / ((long long)a.nx * a.ny));
-    }
-  float acc[MT][2][4];
+    for (int h = 0; h < 2; ++h) base[m][h] = ((2 * warp + m + 1) * kHY + (ly + 2 * h + 1)) * kHX + lx + 1;
+  float acc[2][2][4];
 #pragma unroll
-  for (int m = 0; m < MT; ++m)
+  for (int m = 0; m < 2; ++m)
 #pragma unroll
     for (int n = 0; n < 2; ++n)
 #pragma unroll
       for (int k = 0; k < 4; ++k) acc[m][n][k] = 0.f;
   const int kchunks = a.cin / 16;
-  const long long sxy = (long long)a.nx * a.ny;
   for (int tap = 0; tap < 27; ++tap) {
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const long long off = dx + (long long)a.nx * dy + sxy * dz;
-    const bf16* xp[MT][2];
-    bool ok[MT][2];
-#pragma unroll
-    for (int m = 0; m < MT; ++m)
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int xx = cx[m][h] + dx, yy = cy[m][h] + dy, zz = cz[m][h] + dz;
-        ok[m][h] = row[m][h] >= 0 && xx >= 0 && xx < a.nx && yy >= 0 && yy < a.ny && zz >= 0 && zz < a.nz;
-        xp[m][h] = a.x + (ok[m][h] ? (row[m][h] + off) * a.cin : 0);
-      }
-    const bf16* wt = ws + tap * 16 * ldw;
+    const int off = (tap / 9 - 1) * kHX * kHY + ((tap / 3) % 3 - 1) * kHX + (tap % 3 - 1);
+    const bf16* wt = ws + tap * 16 * ld;
     for (int kc = 0; kc < kchunks; ++kc) {
       const int k0 = kc * 16 + 2 * t;
       uint32_t b[2][2];
 #pragma unroll
       for (int n = 0; n < 2; ++n) {
-        const bf16* wr = wt + (n * 8 + g) * ldw + k0;
+        const bf16* wr = wt + (n * 8 + g) * ld + k0;
         b[n][0] = ld_pair(wr);
         b[n][1] = ld_pair(wr + 8);
       }
 #pragma unroll
-      for (int m = 0; m < MT; ++m) {
-        const uint32_t a0 = ok[m][0] ? ld_pair(xp[m][0] + k0) : 0u;
-        const uint32_t a1 = ok[m][1] ? ld_pair(xp[m][1] + k0) : 0u;
-        const uint32_t a2 = ok[m][0] ? ld_pair(xp[m][0] + k0 + 8) : 0u;
-        const uint32_t a3 = ok[m][1] ? ld_pair(xp[m][1] + k0 + 8) : 0u;
+      for (int m = 0; m < 2; ++m) {
+        const bf16* p0 = xs + (base[m][0] + off) * ld + k0;
+        const bf16* p1 = xs + (base[m][1] + off) * ld + k0;
+        const uint32_t a0 = ld_pair(p0), a1 = ld_pair(p1), a2 = ld_pair(p0 + 8), a3 = ld_pair(p1 + 8);
 #pragma unroll
         for (int n = 0; n < 2; ++n) mma_bf16(acc[m][n], a0, a1, a2, a3, b[n][0], b[n][1]);
       }
     }
   }
 #pragma unroll
-  for (int m = 0; m < MT; ++m)
+  for (int m = 0; m < 2; ++m)
 #pragma unroll
     for (int n = 0; n < 2; ++n) {
       const int c = co0 + n * 8 + 2 * t;
@@ -156,8 +156,9 @@ __global__ void __launch_bounds__(128) k_conv(const ConvArgs a) {
         for (int k = 0; k < 4; ++k) v[k] = fmaxf(v[k], 0.f);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const long long r = row[m][h];
-        if (r < 0) continue;
+        const int xx = x0 + lx, yy = y0 + ly + 2 * h, zz = z0 + 2 * warp + m;
+        if (xx >= a.nx || yy >= a.ny || zz >= a.nz) continue;
+        const long long r = (long long)xx + (long long)a.nx * (yy + (long long)a.ny * zz);
         if (a.y) *reinterpret_cast<__nv_bfloat162*>(a.y + r * a.cout + c) = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
         if (a.yf) { a.yf[r * a.cout + c] = v[2 * h]; a.yf[r * a.cout + c + 1] = v[2 * h + 1]; }
       }
