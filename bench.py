@@ -304,6 +304,19 @@ def run_learned(args):
     n = tr.n
     x = torch.randn(n, 4, device="cuda", dtype=torch.float32)
     y = torch.empty(n, 2, device="cuda", dtype=torch.float32)
+    if args.profile_case:
+        # bounded case for the profilers: 3 forwards and 2 training steps on the bulk Cu
+        # volume (33 + 2 x 22 convolution launches), then exit
+        for _ in range(3):
+            pkg.transec_unet_forward(lp.net, x, y)
+        tgt = torch.randn(n, 2, device="cuda", dtype=torch.float32)
+        for _ in range(2):
+            pkg.transec_unet_train_step(lp.net, x, tgt, 1e-4)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "ok", "workload": "learned"}))
+        lp.close()
+        tr.close()
+        return 0
     for _ in range(max(3, args.warmup)):
         pkg.transec_unet_forward(lp.net, x, y)
     torch.cuda.synchronize()
@@ -397,7 +410,8 @@ def main():
     ap.add_argument("--items", type=int, default=0, help="column solves per step and GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
-                    help="small bounded run for ncu: 32 columns, 40 iterations each, then exit")
+                    help="small bounded run for ncu: 32 columns, 40 iterations each (with "
+                         "--workload learned: 3 forwards and 2 training steps), then exit")
     ap.add_argument("--workload", default="cu_bulk", choices=["cu_bulk", "uneven_batch", "learned"],
                     help="uneven_batch: the 96-cell mixed batch, batched vs looped per cell; "
                          "learned: the U-Net preconditioner's forward and FGMRES gain")
