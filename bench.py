@@ -434,7 +434,7 @@ def main():
 
     from workloads import cu_bulk
     import paper_2208_02783_gb300 as pkg
-    from paper_2208_02783_gb300 import build
+    from paper_2208_02783_gb300 import build, replicas
 
     pkg.load(build.build())
     inst = cu_bulk()
@@ -453,7 +453,9 @@ def main():
             dist.barrier()
 
     def step_items(step):
-        return draw_items(inst, reps, n_rhs, items_per_step, 2000 + 100 * rank + step)
+        # one seeded sample of distinct (E, k, column) items per step, split across ranks
+        ei, k, c = replicas.step_items(len(inst.energies), reps, n_rhs, items_per_step, step, rank, ws)
+        return inst.energies[ei].astype(np.float64), k, c
 
     dev_items = {}
 
@@ -505,12 +507,9 @@ def main():
         iters_total += int(r["iters"].sum().item())
         fails += int((r["status"] != 0).sum().item())
     st = tr.stats()
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, device=dev)
     cols = items_per_step * args.steps * ws
-    col_rate = cols / (ms / 1e3)
+    col_rate = replicas.whole_job_rate(items_per_step * args.steps, ws, ms / 1e3)
     value = 2.0 * col_rate / n_rhs
 
     # parity of the timed form against the plain FP64 form on the first columns of the
@@ -541,11 +540,8 @@ def main():
         t0 = time.perf_counter()
         tr.column_contributions(pe, pk, pc)
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = 2.0 * (items_per_step * args.steps * ws / (e2e_ms / 1e3)) / n_rhs
+    e2e_ms = replicas.max_over_ranks(e2e_ms, device=dev)
+    e2e_value = 2.0 * replicas.whole_job_rate(items_per_step * args.steps, ws, e2e_ms / 1e3) / n_rhs
 
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
@@ -592,7 +588,8 @@ def main():
             "mean_iterations_per_column": iters_total / max(1, cols // ws),
             "failed_columns": fails, "fp64_fallback_columns": int(st.get("fallbacks", 0)), "l2": "working set of the slots (~GBs) exceeds L2; no flush needed",
             "parity_vs_fp64": parity,
-            "sampling": "seeded uniform (energy, k-pair, left-CAP column) per step and rank",
+            "sampling": "one seeded sample of distinct (energy, k-pair, left-CAP column) items per "
+                        "step, split across ranks (rank r takes every N-th item from r)",
         },
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
