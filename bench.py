@@ -38,10 +38,10 @@ WORKLOAD = ("bulk fcc Cu [001] a=6.82, 20x20x480 h=0.341, order 12, V0=1.2 sigma
             "jitter, 64-plane CAPs 0.3 Ha, 8x8 MP k-mesh, 256 energies in E_F+-0.3 Ha, tol 1e-10")
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per point-half of one FP64 stencil launch, from the ncu capture in
-# profiles/k_stencil_fp64_cu_bulk.md (897.7 MB for 12.29 M point-halves); scaled by the
+# profiles/k_stencil_fp64_cu_bulk.md (900.5 MB for 12.29 M point-halves); scaled by the
 # point-halves of each launch for the roofline's traffic.  Reset to None whenever the
 # kernel changes.
-FP64_STENCIL_DRAM_PER_POINT_HALF = 897.7e6 / 12.288e6
+FP64_STENCIL_DRAM_PER_POINT_HALF = 900.5e6 / 12.288e6
 # FP64 ALU roofline: 2 FP64 FMA per clock per SM x 152 SMs x 2070 MHz x 2 flops
 FP64_PEAK_TFLOPS = 2 * 152 * 2.070e9 * 2 / 1e12
 
