@@ -286,8 +286,9 @@ def unet_forward_flops(nvox: int, padded: bool) -> float:
 
 
 def run_learned(args):
-    """Learned right preconditioner (growth form): the U-Net forward on the bulk Cu
-    volume (20x20x480, the network's per-Arnoldi-step cost), timed with CUDA events, and
+    """Learned right preconditioner (an extension of the method): the U-Net forward on
+    the bulk Cu volume (20x20x480, the network's per-Arnoldi-step cost), timed with
+    CUDA events, and
     the FGMRES(30) gain on a 16x16x32 order-4 cell (operator applications and time per
     column with the network on alternate steps, without it, and with the plain FP64
     engine)."""

@@ -258,7 +258,7 @@ int transec_stats(const transec_ctx* ctx, long long* launches, long long* point_
 int transec_stats_reset(transec_ctx* ctx);
 
 /*
- * Learned right preconditioner (NS growth; the paper has no learned component): a
+ * Learned right preconditioner (an extension; the paper has no learned component): a
  * 3D U-Net with 3 levels of 16/32/64 channels, 3x3x3 convolutions (zero padding),
  * ReLU, 2x2x2 average pooling, nearest 2x upsampling and skip concatenation, 4 input
  * channels (Re r, Im r, V, Gamma) and 2 outputs (Re e, Im e).  Its convolutions run as
