@@ -36,6 +36,9 @@ METRIC = "converged (E,k) T(E) solves/sec at |ΔT|≤1e-6 vs plain FP64 GPU; ste
 UNIT = "(E,k) solves/s"
 WORKLOAD = ("bulk fcc Cu [001] a=6.82, 20x20x480 h=0.341, order 12, V0=1.2 sigma=0.9 +-2% "
             "jitter, 64-plane CAPs 0.3 Ha, 8x8 MP k-mesh, 256 energies in E_F+-0.3 Ha, tol 1e-10")
+WORKLOAD_RH = ("Rh periodic point contact [001] a=7.18, 3x3 cells, 60x60x512 h=0.359, order 12, "
+               "V0=1.4 sigma=0.95, hyperboloid neck r0=4, 1% vacancies, 64-plane CAPs 0.3 Ha, "
+               "4x4 MP k-mesh, 512 energies in E_F+-0.3 Ha, tol 1e-10")
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per point-half of one FP64 stencil launch, from the ncu capture in
 # profiles/k_stencil_fp64_cu_bulk.md (900.5 MB for 12.29 M point-halves); scaled by the
@@ -413,8 +416,10 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small bounded run for ncu: 32 columns, 40 iterations each (with "
                          "--workload learned: 3 forwards and 2 training steps), then exit")
-    ap.add_argument("--workload", default="cu_bulk", choices=["cu_bulk", "uneven_batch", "learned"],
-                    help="uneven_batch: the 96-cell mixed batch, batched vs looped per cell; "
+    ap.add_argument("--workload", default="cu_bulk",
+                    choices=["cu_bulk", "rh_point_contact", "uneven_batch", "learned"],
+                    help="rh_point_contact: the 60x60x512 Rh point contact (use --items 16); "
+                         "uneven_batch: the 96-cell mixed batch, batched vs looped per cell; "
                          "learned: the U-Net preconditioner's forward and FGMRES gain")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -433,12 +438,14 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    from workloads import cu_bulk
+    from workloads import cu_bulk, rh_point_contact
     import paper_2208_02783_gb300 as pkg
     from paper_2208_02783_gb300 import build, replicas
 
     pkg.load(build.build())
-    inst = cu_bulk()
+    rh = args.workload == "rh_point_contact"
+    inst = rh_point_contact() if rh else cu_bulk()
+    workload_name = WORKLOAD_RH if rh else WORKLOAD
     g = inst.grid
     n_rhs = inst.n_rhs
     reps = k_representatives(inst.kfrac)
@@ -559,7 +566,7 @@ def main():
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS,
                 "traffic": (FP64_STENCIL_DRAM_PER_POINT_HALF * pa / launches_s
-                            if FP64_STENCIL_DRAM_PER_POINT_HALF else None),
+                            if FP64_STENCIL_DRAM_PER_POINT_HALF and not rh else None),
                 "kernel": "k_stencil<double,6> (FP64 stencil fused with p = r + beta p and the pairing dot)",
                 "per_launch": {"flops": flops / launches_s, "bytes": bytes_alg / launches_s,
                                "ms": st["stencil_ms"] / launches_s},
@@ -581,7 +588,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "c128" if prec == pkg.PREC_FP64 else "c64+f64",
         "data": "synthetic",
         "config": {
-            "workload": WORKLOAD, "form": ("FP64 transpose BiCG (+-k)" if prec == pkg.PREC_FP64
+            "workload": workload_name, "form": ("FP64 transpose BiCG (+-k)" if prec == pkg.PREC_FP64
                                            else "complex FP32 BiCG with FP64 scalars and residual replacement"),
             "column_solves_per_step_per_gpu": items_per_step, "slots": slots,
             "column_solves_per_s": col_rate, "n_rhs_per_Ek": n_rhs,
