@@ -59,3 +59,24 @@ def test_invalid_geometry_rejected_before_device_use():
     assert ei.value.status == pkg.EINVAL
     with pytest.raises(pkg.TransecError):
         pkg.transec_create(0, 4, 8, 0.5, 0.5, 0.5, 2)
+
+
+def test_network_and_fgmres_arguments_rejected_before_device_use():
+    import ctypes as C
+
+    lib = pkg.load()
+    out = C.c_void_p()
+    # the network needs every dimension a positive multiple of 4 (two 2x poolings)
+    for dims in ((6, 8, 8), (8, 8, 2), (0, 8, 8), (8, -4, 8)):
+        assert lib.transec_unet_create(C.byref(out), 0, *dims, 0) == pkg.EINVAL
+        assert out.value is None
+    assert lib.transec_unet_create(None, 0, 8, 8, 8, 0) == pkg.EINVAL
+    n = C.c_longlong()
+    assert lib.transec_unet_n_params(None, C.byref(n)) == pkg.EINVAL
+    assert lib.transec_unet_dims(None, None, None, None) == pkg.EINVAL
+    assert lib.transec_unet_forward(None, None, None, 0) == pkg.EINVAL
+    assert lib.transec_unet_train_step(None, None, None, 0.0, None, None, 0) == pkg.EINVAL
+    assert lib.transec_unet_train_operator(None, None, 1, 10, 0.0, 1.0, 1e-3, 0, None) == pkg.EINVAL
+    assert lib.transec_fgmres_columns(None, None, 2, 1, None, None, None, 30, 100, None, None, None,
+                                      None) == pkg.EINVAL
+    lib.transec_unet_destroy(None)  # ignored
