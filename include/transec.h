@@ -291,7 +291,8 @@ int transec_unet_dims(const transec_unet* u, int* nx, int* ny, int* nz);
 const char* transec_unet_last_error(const transec_unet* u);
 
 /*
- * Fit the network to the operator family of `ctx` (same volume): `steps` Adam steps
+ * Fit the network to the operator family A(E, k) = E - H_k + i Gamma of `ctx`
+ * (Sec. II.A; same volume): `steps` Adam steps
  * at learning rate lr, each on one pair (r, e) with r = A(E, k) e, E uniform in
  * [e_lo, e_hi] and k uniform over the mesh, all drawn from `seed`.  source 0: e is a
  * seeded random complex field (standard normals smoothed by 0, 1, 2, 3, 5 or 8 passes
@@ -314,7 +315,8 @@ int transec_unet_train_operator(transec_ctx* ctx, transec_unet* net, int source,
  * net_every-th Arnoldi step (1: every step; 2: alternating with the identity) and the
  * identity on the others; net == NULL gives plain restarted GMRES.  Item i solves
  * A(energies[i], k_{ik[i]}) x = e_j for the cols[i]-th left-CAP column to
- * ||e_j - A x|| <= opts.tol in FP64 and writes t_out[i] = t_j.  A column whose residual
+ * ||e_j - A x|| <= opts.tol in FP64 and writes t_out[i] = t_j, the column's share of
+ * T(E, k) (Sec. II.A; the same quantity as transec_column_contributions).  A column whose residual
  * has not halved over 10 restart cycles, that reaches maxit operator applications, or
  * whose Hessenberg matrix turns singular (a zero preconditioned direction) is solved
  * again by the plain FP64 Krylov engine (fallback_out[i] = 1).  iters_out
