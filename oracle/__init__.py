@@ -4,7 +4,7 @@ THIS PACKAGE IS TEST INFRASTRUCTURE.  It is a plain, slow, complex128 restatemen
 what the GPU library computes, written from the paper (Zhu, Feldman & Dunham,
 "Highly parallelizable electronic transport calculations in periodic Rhodium and
 Copper nanostructures", arXiv 2208.02783) so that the CUDA path can be checked
-against it.  Only the tests, the graft smoke check and the benchmark's CPU-baseline
+against it.  Only the tests, `__graft_entry__.smoke()` and the benchmark's CPU-baseline
 leg may import it; the library never does, and it shares no code with the library
 (its only shared dependency is the seeded input package ``workloads``).
 
@@ -12,8 +12,9 @@ Modules
 -------
 fd           central finite-difference coefficients (exact rationals)
 hamiltonian  H_k with Bloch-phased lateral faces and A(E, k) in CSR form
-transmission T(E, k) by dense LU, sparse LU or plain COCG/BiCGStab; k-average
+transmission T(E, k) by dense LU, sparse LU or plain COCG / transpose BiCG; k-average
 closed_form  separable V = 0 transmission and open-channel (mode) counting
+unet         NumPy forward/backward of the learned preconditioner's network
 
 Every function is pinned by tests/test_oracle_*.py against facts fixed by the paper
 or by mathematics (polynomial exactness, Hermiticity, separable closed form, the
