@@ -329,6 +329,20 @@ int transec_fgmres_columns(transec_ctx* ctx, transec_unet* net, int net_every, i
                            int* status_out, int* fallback_out);
 void transec_unet_destroy(transec_unet* u);
 
+/*
+ * One left-CAP column at ne energies by a multi-shift transpose BiCG: A(E, k) differs
+ * from A(E0, k) by (E - E0) times the identity (Sec. II.A), so one Krylov run seeded at
+ * the middle energy E0 yields every energy's column through collinear residuals, with
+ * the per-energy iterates kept on the Gamma_R planes the trace reads.  Writes
+ * t_out[s] = t_j and, if not NULL, t_minus_out[s] = t_j at -k (from the shadow system,
+ * Sec. II.B) for energies[s]; iters_out[s] = seed iterations at which energy s
+ * converged (||e_j - A x|| <= opts.tol, from the seed residual); status_out[s] its
+ * status.  Host arrays; 1 <= ne <= 4096.  A host-driven single-column form of the
+ * method.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA; per-energy ENOCONV / EBREAKDOWN.
+ */
+int transec_shifted_column(transec_ctx* ctx, int ne, const double* energies, int ik, int64_t col,
+                           double* t_out, double* t_minus_out, int* iters_out, int* status_out);
+
 /* Message of the last failure on this context ("" if none).  Valid until the next
  * call on the same context. */
 const char* transec_last_error(const transec_ctx* ctx);

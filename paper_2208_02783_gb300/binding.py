@@ -95,6 +95,7 @@ _SIGS = {
                                              C.c_ulonglong, _P]),
     "transec_fgmres_columns": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P,
                                          _P]),
+    "transec_shifted_column": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_longlong, _P, _P, _P, _P]),
     "transec_unet_destroy": (None, [_P]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
@@ -466,3 +467,18 @@ def transec_fgmres_columns(ctx, u, energies, ik, cols, restart=30, maxit=20000, 
                                        vp(t), vp(it), vp(so), vp(fb))
     _check(ctx, st, "transec_fgmres_columns", allow=(ENOCONV, EBREAKDOWN))
     return t, it, so, fb
+
+
+def transec_shifted_column(ctx, energies, ik, col):
+    """One column at several energies by the multi-shift transpose BiCG; returns
+    (t, t_minus, iters, status) host arrays in the order of ``energies``."""
+    e = np.ascontiguousarray(energies, np.float64)
+    n = e.size
+    t = np.zeros(n)
+    tm = np.zeros(n)
+    it = np.zeros(n, np.int32)
+    so = np.zeros(n, np.int32)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    st = load().transec_shifted_column(ctx, n, vp(e), int(ik), int(col), vp(t), vp(tm), vp(it), vp(so))
+    _check(ctx, st, "transec_shifted_column", allow=(ENOCONV, EBREAKDOWN))
+    return t, tm, it, so

@@ -79,4 +79,5 @@ def test_network_and_fgmres_arguments_rejected_before_device_use():
     assert lib.transec_unet_train_operator(None, None, 1, 10, 0.0, 1.0, 1e-3, 0, None) == pkg.EINVAL
     assert lib.transec_fgmres_columns(None, None, 2, 1, None, None, None, 30, 100, None, None, None,
                                       None) == pkg.EINVAL
+    assert lib.transec_shifted_column(None, 1, None, 0, 0, None, None, None, None) == pkg.EINVAL
     lib.transec_unet_destroy(None)  # ignored
