@@ -17,7 +17,7 @@ from .binding import (  # noqa: F401
     transec_get_solver, transec_last_error, transec_n_rhs, transec_set_abc,
     transec_set_kmesh, transec_set_potential, transec_set_solver, transec_stats,
     transec_stats_reset, transec_status_string, transec_trace, transec_transmission,
-    transec_version, transec_fgmres_columns, transec_unet_create, transec_unet_destroy,
+    transec_version, transec_fgmres_columns, transec_shifted_column, transec_unet_create, transec_unet_destroy,
     transec_unet_dims, transec_unet_forward, transec_unet_get_params, transec_unet_n_params,
     transec_unet_set_params, transec_unet_train_operator, transec_unet_train_step,
 )
@@ -118,6 +118,11 @@ class Transec:
             st = np.zeros(n, np.int32)
         rc = transec_column_contributions(self.ctx, energies, ik, cols, t, tm, it, st)
         return {"t": t, "t_minus": tm, "iters": it, "status": st, "rc": rc}
+
+    def shifted_column(self, energies, ik, col):
+        """One left-CAP column at many energies in one multi-shift Krylov run."""
+        t, tm, it, st = transec_shifted_column(self.ctx, energies, ik, col)
+        return {"t": t, "t_minus": tm, "iters": it, "status": st}
 
     def apply(self, energy, ik, x, conj_k=False):
         x = np.ascontiguousarray(x, np.complex128)
