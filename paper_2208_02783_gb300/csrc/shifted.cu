@@ -169,6 +169,18 @@ struct DevScope {
   }
 };
 
+// Ranking of per-energy statuses for the call's return value (the same order as the
+// other solve entry points: not converged < breakdown < timeout < anything else).
+int shifted_severity(int code) {
+  switch (code) {
+    case TRANSEC_OK: return 0;
+    case TRANSEC_ENOCONV: return 1;
+    case TRANSEC_EBREAKDOWN: return 2;
+    case TRANSEC_ETIMEOUT: return 3;
+    default: return 4;
+  }
+}
+
 int sh_fail(transec_ctx* ctx, int code, const std::string& msg) {
   ctx->err = msg;
   return code;
@@ -330,7 +342,10 @@ extern "C" int transec_shifted_column(transec_ctx* ctx, int ne, const double* en
     if (live == 0) break;
     cplx rho_new;
     if ((e = dot(rs, r, 0, rho_new)) != cudaSuccess) break;
-    if (std::abs(rho) == 0) {
+    // BiCG breaks down when the new bilinear form <r~, r> vanishes (or is not finite)
+    // while the residuals are not yet small: beta = rho_new / rho would then be zero
+    // and every later alpha with it
+    if (std::abs(rho_new) == 0 || !std::isfinite(std::abs(rho_new))) {
       for (int s = 0; s < ne; ++s)
         if (active[s]) status[s] = TRANSEC_EBREAKDOWN;
       break;
@@ -395,7 +410,7 @@ extern "C" int transec_shifted_column(transec_ctx* ctx, int ne, const double* en
     if (t_minus_out) t_minus_out[s] = ok ? 4.0 * glj * b : std::nan("");
     if (iters_out) iters_out[s] = ok ? its[s] : n_it;
     if (status_out) status_out[s] = status[s];
-    if (!ok && (worst == TRANSEC_OK || status[s] < worst)) worst = status[s];
+    if (!ok && shifted_severity(status[s]) > shifted_severity(worst)) worst = status[s];
   }
   if (worst != TRANSEC_OK) ctx->err = "some energies failed (see status_out)";
   return worst;

@@ -197,3 +197,40 @@ def test_column_contributions_definition():
 
 def test_k_average():
     assert np.allclose(k_average([[1.0, 3.0], [2.0, 2.0]], [0.25, 0.75]), [2.5, 2.0])
+
+
+@pytest.mark.parametrize(
+    "dims,order,kf",
+    [
+        ((7, 6, 40, 0.45, 8, 10), 8, (0.23, -0.37)),
+        ((3, 4, 30, 0.45, 12, 8), 12, (0.31, 0.12)),  # order 12 on a 3x4 cell: several wraps
+    ],
+)
+def test_bicg_shadow_solution_is_the_minus_k_column(dims, order, kf):
+    """The transpose BiCG's shadow iterate y solves A(E, k)^T y = e_j, and
+    A(E, k)^T = A(E, -k) because H_{-k} = H_k^* with H_k Hermitian (Sec. II.B).  So y
+    must be the dense-LU column of G(E, -k) and its trace t_j(-k); the full-size golden
+    t_minus values rest on this."""
+    from oracle.transmission import bicg_transpose, solve_dense
+
+    nx, ny, nz, h, _, ncap = dims
+    inst = small_instance(nx, ny, nz, h, order, ncap, v_amp=0.6, seed=17)
+    g = inst.grid
+    e = 0.45
+    cols = left_support(g, inst.gamma_l)[::23][:6]
+    a = system_matrix(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf)
+    b = np.zeros((g.n, cols.size), complex)
+    b[cols, np.arange(cols.size)] = 1.0
+    x, y, its = bicg_transpose(a, b, 1e-12, 20000)
+    assert np.all(its > 0)
+    mk = (-kf[0], -kf[1])
+    xd = solve_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf, cols)
+    yd = solve_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, mk, cols)
+    scale = np.abs(yd).max()
+    assert np.abs(x - xd).max() <= 1e-9 * scale
+    assert np.abs(y - yd).max() <= 1e-9 * scale
+    # y is not the +k column (the check has teeth at k != 0)
+    assert np.abs(y - xd).max() > 1e-3 * scale
+    ty = column_contributions(g, inst.gamma_l, inst.gamma_r, cols, y)
+    _, tref = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, mk, cols)
+    assert np.abs(ty - tref).max() <= 1e-10
