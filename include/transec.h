@@ -343,6 +343,67 @@ void transec_unet_destroy(transec_unet* u);
 int transec_shifted_column(transec_ctx* ctx, int ne, const double* energies, int ik, int64_t col,
                            double* t_out, double* t_minus_out, int* iters_out, int* status_out);
 
+/*
+ * Sampled columns at a whole window of energies by the multi-shift engine (the slot
+ * engine of transec_column_contributions with every run serving ne energies):
+ * A(E, k) = A(E0, k) + (E - E0) 1 (Sec. II.A), so one transpose-BiCG run seeded at the
+ * middle energy E0 of the window yields every energy's column of G(E, k) e_j and, from
+ * its shadow system, of G(E, -k) e_j (A(E, k)^T = A(E, -k), Sec. II.B).  The per-energy
+ * iterates are kept only on the Gamma_R planes the trace reads.  Item i is the
+ * cols[i]-th left-CAP column at k index ik[i]; for every energy s it writes
+ * t_out[i*ne + s] = t_j(E_s, k), t_minus_out[i*ne + s] = t_j(E_s, -k) (may be NULL),
+ * iters_out[i*ne + s] = seed iterations at which energy s converged
+ * (||e_j - A(E_s) x|| <= opts.tol, from the collinear seed residual) and
+ * status_out[i*ne + s] (may be NULL).  Runs retire and refill on the GPU as in the
+ * plain engine (opts.slots runs in flight, 0 = chosen from the grid size and free
+ * memory); the whole solve is one graph launch with a device-side loop unless
+ * opts.profile or opts.host_loop is set.  Host arrays; 1 <= ne <= 1024.  Failed
+ * (E, item) results get t = NaN and the call returns the most severe status.
+ * Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT.
+ */
+int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, int nitems,
+                            const int* ik, const int64_t* cols, double* t_out, double* t_minus_out,
+                            int* iters_out, int* status_out);
+
+/*
+ * Full-trace transmission T(E, k) and T(E, -k) for a window of energies from a
+ * two-sided randomized sketch of M = Gamma_R^1/2 G Gamma_L^1/2 (Sec. II.A:
+ * T = 4 Tr[Gamma_L G^dagger Gamma_R G] = 4 ||M||_F^2).  M has numerical rank about the
+ * number of open (and barely closed) channels at (E, k) (Sec. III), far below its
+ * n_rhs columns, so instead of n_rhs unit columns the library solves, for each k of
+ * ik[0..nrep-1], s_left runs with random right-hand sides Gamma_L^1/2 omega and s_right
+ * runs with Gamma_R^1/2 psi (omega, psi: unit-modulus random phases from `seed`, by
+ * splitmix64), every run a multi-shift transpose BiCG over the whole window (as in
+ * transec_shifted_columns).  The LEFT runs give Y = M Omega, the RIGHT runs' shadow
+ * systems W = Psi^T M (and the other halves the same pair at -k); per energy and
+ * sign of k the library forms Q = orth(Y), X = (Psi^T Q)^+ W and T = 4 ||X||_F^2 (the
+ * two-sided low-rank approximation of Tropp, Yurtsever, Udell & Cevher, SIAM J. Matrix
+ * Anal. Appl. 2017), exact to rounding when the numerical rank of M is at most s_left.
+ * T_out[r*ne + s] = T(E_s, k_{ik[r]}); T_minus_out[r*ne + s] = T(E_s, -k) computed from
+ * the other halves (equal to T(E_s, k) in exact arithmetic, Sec. II.B: an independent
+ * estimate, so |T - T_minus| gauges the sketch error); rank_out = directions of Y kept;
+ * status_out per result; iters_out = seed iterations at which the energy converged in
+ * its slowest run.  1 <= s_left <= 32, s_left <= s_right <= 64, 1 <= ne <= 1024.  All
+ * nrep * (s_left + s_right) runs are in flight at once (no refill).  Host arrays.
+ * Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT; per-result ENOCONV / EBREAKDOWN with
+ * T = NaN.
+ */
+int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies, int nrep,
+                                const int* ik, int s_left, int s_right, unsigned long long seed,
+                                double* T_out, double* T_minus_out, int* rank_out, int* status_out,
+                                int* iters_out);
+
+/*
+ * Counters of the multi-shift engine since the last transec_stats_reset: seed
+ * iterations summed over runs, per-shift point updates (kept points x halves x
+ * iterations of each shift), and with opts.profile set the event-timed stencil and
+ * shifted-update kernels (ms, launches) and the sketch reduction (ms).  Any output
+ * may be NULL.
+ */
+int transec_sweep_stats(const transec_ctx* ctx, long long* iters, long long* shift_points,
+                        double* stencil_ms, long long* stencil_launches, double* shift_ms,
+                        long long* shift_launches, double* reduce_ms);
+
 /* Message of the last failure on this context ("" if none).  Valid until the next
  * call on the same context. */
 const char* transec_last_error(const transec_ctx* ctx);

@@ -17,7 +17,8 @@ from .binding import (  # noqa: F401
     transec_get_solver, transec_last_error, transec_n_rhs, transec_set_abc,
     transec_set_kmesh, transec_set_potential, transec_set_solver, transec_stats,
     transec_stats_reset, transec_status_string, transec_trace, transec_transmission,
-    transec_version, transec_fgmres_columns, transec_shifted_column, transec_unet_create, transec_unet_destroy,
+    transec_version, transec_fgmres_columns, transec_shifted_column, transec_shifted_columns,
+    transec_sweep_stats, transec_transmission_sketch, transec_unet_create, transec_unet_destroy,
     transec_unet_dims, transec_unet_forward, transec_unet_get_params, transec_unet_n_params,
     transec_unet_set_params, transec_unet_train_operator, transec_unet_train_step,
 )
@@ -123,6 +124,21 @@ class Transec:
         """One left-CAP column at many energies in one multi-shift Krylov run."""
         t, tm, it, st = transec_shifted_column(self.ctx, energies, ik, col)
         return {"t": t, "t_minus": tm, "iters": it, "status": st}
+
+    def shifted_columns(self, energies, ik, cols):
+        """Sampled left-CAP columns, each at every energy of the window, by the
+        multi-shift engine: arrays of shape (len(cols), len(energies))."""
+        t, tm, it, st = transec_shifted_columns(self.ctx, energies, ik, cols)
+        return {"t": t, "t_minus": tm, "iters": it, "status": st}
+
+    def transmission_sketch(self, energies, ik, s_left=16, s_right=32, seed=0):
+        """Full-trace T(E, k) and T(E, -k) for the k indices ``ik`` over a window of
+        energies from the two-sided sketch: arrays of shape (len(ik), len(energies))."""
+        T, tm, rk, st, it = transec_transmission_sketch(self.ctx, energies, ik, s_left, s_right, seed)
+        return {"T": T, "T_minus": tm, "rank": rk, "status": st, "iters": it}
+
+    def sweep_stats(self) -> dict:
+        return transec_sweep_stats(self.ctx)
 
     def apply(self, energy, ik, x, conj_k=False):
         x = np.ascontiguousarray(x, np.complex128)

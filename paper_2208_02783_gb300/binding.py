@@ -96,6 +96,12 @@ _SIGS = {
     "transec_fgmres_columns": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, C.c_int, C.c_int, _P, _P, _P,
                                          _P]),
     "transec_shifted_column": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_longlong, _P, _P, _P, _P]),
+    "transec_shifted_columns": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "transec_transmission_sketch": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_ulonglong,
+                                              _P, _P, _P, _P, _P]),
+    "transec_sweep_stats": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_longlong), C.POINTER(C.c_double)]),
     "transec_unet_destroy": (None, [_P]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
@@ -482,3 +488,49 @@ def transec_shifted_column(ctx, energies, ik, col):
     st = load().transec_shifted_column(ctx, n, vp(e), int(ik), int(col), vp(t), vp(tm), vp(it), vp(so))
     _check(ctx, st, "transec_shifted_column", allow=(ENOCONV, EBREAKDOWN))
     return t, tm, it, so
+
+
+def transec_shifted_columns(ctx, energies, ik, cols):
+    """Columns at a window of energies by the multi-shift engine; returns
+    (t, t_minus, iters, status) host arrays of shape (nitems, ne)."""
+    e = np.ascontiguousarray(energies, np.float64)
+    k = np.ascontiguousarray(ik, np.int32)
+    c = np.ascontiguousarray(cols, np.int64)
+    ne, n = e.size, k.size
+    if c.size != n:
+        raise ValueError("ik and cols differ in length")
+    t = np.zeros((n, ne))
+    tm = np.zeros((n, ne))
+    it = np.zeros((n, ne), np.int32)
+    so = np.zeros((n, ne), np.int32)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    st = load().transec_shifted_columns(ctx, ne, vp(e), n, vp(k), vp(c), vp(t), vp(tm), vp(it), vp(so))
+    _check(ctx, st, "transec_shifted_columns", allow=(ENOCONV, EBREAKDOWN))
+    return t, tm, it, so
+
+
+def transec_transmission_sketch(ctx, energies, ik, s_left=16, s_right=32, seed=0):
+    """Full-trace T(E, k) and T(E, -k) by the two-sided sketch; returns
+    (T, T_minus, rank, status, iters) host arrays of shape (len(ik), ne)."""
+    e = np.ascontiguousarray(energies, np.float64)
+    k = np.ascontiguousarray(ik, np.int32)
+    ne, nr = e.size, k.size
+    T = np.zeros((nr, ne))
+    Tm = np.zeros((nr, ne))
+    rk = np.zeros((nr, ne), np.int32)
+    so = np.zeros((nr, ne), np.int32)
+    it = np.zeros((nr, ne), np.int32)
+    vp = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    st = load().transec_transmission_sketch(ctx, ne, vp(e), nr, vp(k), int(s_left), int(s_right), int(seed),
+                                            vp(T), vp(Tm), vp(rk), vp(so), vp(it))
+    _check(ctx, st, "transec_transmission_sketch", allow=(ENOCONV, EBREAKDOWN))
+    return T, Tm, rk, so, it
+
+
+def transec_sweep_stats(ctx) -> dict:
+    v = [C.c_longlong(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(),
+         C.c_double()]
+    _check(ctx, load().transec_sweep_stats(ctx, *[C.byref(x) for x in v]), "transec_sweep_stats")
+    keys = ("iters", "shift_points", "stencil_ms", "stencil_launches", "shift_ms", "shift_launches",
+            "reduce_ms")
+    return {k: x.value for k, x in zip(keys, v)}

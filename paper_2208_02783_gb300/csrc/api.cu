@@ -1433,6 +1433,23 @@ int transec_stats_reset(transec_ctx* ctx) {
   ctx->fallbacks = 0;
   ctx->stencil32_ms = 0;
   ctx->stencil32_launches = ctx->point_applies32 = 0;
+  ctx->sweep_iters = ctx->sweep_shift_points = 0;
+  ctx->sweep_stencil_ms = ctx->sweep_shift_ms = ctx->sweep_update_ms = ctx->sweep_reduce_ms = 0;
+  ctx->sweep_stencil_launches = ctx->sweep_shift_launches = 0;
+  return TRANSEC_OK;
+}
+
+int transec_sweep_stats(const transec_ctx* ctx, long long* iters, long long* shift_points,
+                        double* stencil_ms, long long* stencil_launches, double* shift_ms,
+                        long long* shift_launches, double* reduce_ms) {
+  if (!ctx) return TRANSEC_EINVAL;
+  if (iters) *iters = ctx->sweep_iters;
+  if (shift_points) *shift_points = ctx->sweep_shift_points;
+  if (stencil_ms) *stencil_ms = ctx->sweep_stencil_ms;
+  if (stencil_launches) *stencil_launches = ctx->sweep_stencil_launches;
+  if (shift_ms) *shift_ms = ctx->sweep_shift_ms;
+  if (shift_launches) *shift_launches = ctx->sweep_shift_launches;
+  if (reduce_ms) *reduce_ms = ctx->sweep_reduce_ms;
   return TRANSEC_OK;
 }
 
@@ -1442,6 +1459,7 @@ void transec_destroy(transec_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard dg(ctx->device);
   if (ctx->s) cudaStreamSynchronize(ctx->s);
+  transec::sweep_release(ctx);
   ctx->e64.release();
   ctx->e32.release();
   cudaFree(ctx->mx_x); cudaFree(ctx->mx_q); cudaFree(ctx->mx_p);

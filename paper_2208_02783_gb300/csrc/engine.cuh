@@ -13,6 +13,10 @@ struct transec_ctx;
 
 namespace transec {
 
+// Device buffers of the multi-shift engine (sweep.cu), kept between calls.
+struct SweepBufs;
+void sweep_release(transec_ctx* ctx);
+
 // Device buffers and launch shape of one slot engine (one arithmetic type T, one
 // number of halves H).  Buffers are kept between calls and grown on demand.
 template <typename T>
@@ -105,4 +109,10 @@ struct transec_ctx {
   double stencil32_ms = 0;
   long long stencil32_launches = 0, point_applies32 = 0;
   std::vector<cudaEvent_t> prof_ev;  // 4 per iteration of a chunk when profiling
+  transec::SweepBufs* sweep = nullptr;  // multi-shift engine buffers (sweep.cu)
+  // multi-shift engine counters since the last transec_stats_reset: seed iterations
+  // summed over runs, per-shift point updates, and event-timed kernel ms (profile)
+  long long sweep_iters = 0, sweep_shift_points = 0;
+  double sweep_stencil_ms = 0, sweep_shift_ms = 0, sweep_update_ms = 0, sweep_reduce_ms = 0;
+  long long sweep_stencil_launches = 0, sweep_shift_launches = 0;
 };

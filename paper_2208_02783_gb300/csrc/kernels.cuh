@@ -320,10 +320,26 @@ __global__ void __launch_bounds__(StencilMax<T>::threads, StencilMax<T>::blocks)
 // vector update: x += alpha p, r -= alpha q, partial <r, r> and ||r_h||^2
 // ---------------------------------------------------------------------------------
 
+// alpha = rho / sigma of one slot, sigma summed from the stencil's per-block partials
+// in a fixed order; called by one full warp, the value is valid in every lane.
+__device__ inline double2 slot_alpha(const double* sp, int nblk, double2 rho) {
+  const int lane = threadIdx.x & 31;
+  double sx = 0.0, sy = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    sx += sp[2 * b];
+    sy += sp[2 * b + 1];
+  }
+  sx = warp_sum(sx);
+  sy = warp_sum(sy);
+  sx = __shfl_sync(0xffffffffu, sx, 0);
+  sy = __shfl_sync(0xffffffffu, sy, 0);
+  return cdiv(rho, make_double2(sx, sy));
+}
+
 template <typename T>
 struct UpdateArgs {
   using CT = typename Cx<T>::type;
-  CT* x;
+  CT* x;                   // NULL: no solution update (multi-shift seed)
   CT* r;
   const CT* p;
   const CT* q;
@@ -346,16 +362,8 @@ __global__ void __launch_bounds__(256) k_update(const UpdateArgs<T> a) {
   if (stp->status != SLOT_ACTIVE) return;
   const long long n = a.insts ? a.insts[stp->inst].g.n : a.n;
   if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    double sx = 0.0, sy = 0.0;
-    const double* sp = a.sig_part + (size_t)slot * a.sig_nblk * 2;
-    for (int b = lane; b < a.sig_nblk; b += 32) {
-      sx += sp[2 * b];
-      sy += sp[2 * b + 1];
-    }
-    sx = warp_sum(sx);
-    sy = warp_sum(sy);
-    if (lane == 0) s_alpha = cdiv(stp->rho, make_double2(sx, sy));
+    const double2 al = slot_alpha(a.sig_part + (size_t)slot * a.sig_nblk * 2, a.sig_nblk, stp->rho);
+    if (threadIdx.x == 0) s_alpha = al;
   }
   __syncthreads();
   const CT al = cfrom<CT>(s_alpha);
@@ -369,13 +377,17 @@ __global__ void __launch_bounds__(256) k_update(const UpdateArgs<T> a) {
     for (int h = 0; h < 2; ++h) {
       if (h >= a.H) break;
       const long long off = base + (long long)h * n + i;
-      const CT pp = a.p[off], qq = a.q[off];
-      CT xx = a.x[off], rr = a.r[off];
-      xx.x += al.x * pp.x - al.y * pp.y;
-      xx.y += al.x * pp.y + al.y * pp.x;
+      const CT qq = a.q[off];
+      CT rr = a.r[off];
+      if (a.x) {  // the multi-shift engine keeps no seed solution
+        const CT pp = a.p[off];
+        CT xx = a.x[off];
+        xx.x += al.x * pp.x - al.y * pp.y;
+        xx.y += al.x * pp.y + al.y * pp.x;
+        a.x[off] = xx;
+      }
       rr.x -= al.x * qq.x - al.y * qq.y;
       rr.y -= al.x * qq.y + al.y * qq.x;
-      a.x[off] = xx;
       a.r[off] = rr;
       rv[h] = rr;
     }

@@ -1,0 +1,1290 @@
+// Multi-shift slot engine: many transpose-BiCG runs in flight on the GPU, each run
+// serving a whole window of energies at once.
+//
+// For fixed k, A(E, k) = A(E0, k) + (E - E0) 1 (Sec. II.A: G(E) = [E - H_k + i Gamma]^-1),
+// so every energy of a window shares the Krylov space of a seed energy E0.  A run
+// iterates the seed's transpose BiCG (A x = b with the shadow system A^T y = b;
+// A(E, k)^T = A(E, -k), Sec. II.B) and carries, for every shift sigma = E - E0, the
+// collinear-residual scalars pi_sigma and the shifted iterates, kept only on the grid
+// planes the result reads:
+//
+//   pi_{n+1}     = (1 + alpha_n sigma) pi_n + (alpha_n beta_{n-1} / alpha_{n-1}) (pi_n - pi_{n-1})
+//   p_sigma,n    = r_n / pi_n + (pi_{n-1} / pi_n)^2 beta_{n-1} p_sigma,n-1
+//   x_sigma,n+1  = x_sigma,n + (alpha_n pi_n / pi_{n+1}) p_sigma,n
+//
+// (the shadow iterates y_sigma likewise from the seed's shadow residual).  A shift is
+// converged once max(||r||, ||r~||) / |pi_sigma| <= tol ||b||; it then stops changing.
+// The seed runs until every shift of its window has converged.
+//
+// Runs are items of a device-side queue (slots retire and refill as in the plain
+// engine) of three kinds:
+//   UNIT   b = e_j for a left-CAP column j; the result is t_j(E) and t_j(E, -k) for
+//          every energy of the window (read on the Gamma_R planes);
+//   LEFT   b = Gamma_L^1/2 omega for a random phase vector omega on the left-CAP
+//          support; the Gamma_R planes of x and y are kept;
+//   RIGHT  b = Gamma_R^1/2 psi on the right-CAP support; the Gamma_L planes are kept.
+// LEFT and RIGHT runs of one k form a two-sided sketch of M = Gamma_R^1/2 G Gamma_L^1/2
+// (Sec. II.A: T = 4 Tr[Gamma_L G^dagger Gamma_R G] = 4 ||M||_F^2): the primal halves of
+// the LEFT runs give Y = M Omega, the shadow halves of the RIGHT runs give
+// W = Psi^T M (both at +k; the other halves give the same pair at -k).  k_ms_gn then
+// forms, per energy and sign of k, the low-rank estimate of Tropp, Yurtsever, Udell &
+// Cevher (SIAM J. Matrix Anal. Appl. 38, 2017): Q = orth(Y), X = (Psi^T Q)^+ W,
+// T = 4 ||X||_F^2, exact when the numerical rank of M (about the number of open
+// channels) is below the sketch size.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+
+namespace transec {
+template <typename T>
+cudaError_t prepare_stencil(int R, size_t smem);
+}
+
+using namespace transec;
+
+namespace transec {
+
+enum RunKind : int { RUN_UNIT = 0, RUN_LEFT = 1, RUN_RIGHT = 2 };
+
+// Per-run state beside the seed's Slot.
+struct MsSlot {
+  double2 alpha;       // alpha_n of the current iteration
+  double2 alpha_prev;  // alpha_{n-1} (1 before the first iteration)
+  double bnorm;        // ||b||_2
+  int kind;            // RunKind
+  int rep;             // sketch: group (k representative) of the run
+  int idx;             // sketch: index of the random vector within its kind
+  int pad[3];
+};
+
+// Per-run, per-shift state.
+struct MsShift {
+  double2 pi, pi_prev, pi_next;
+  int active;   // 1 while the shift iterates
+  int status;   // kOK, kENOCONV or kEBREAKDOWN once the shift stopped
+  int conv_it;  // seed iteration at which it stopped
+  int pad;
+};
+
+// Coefficients of one iteration's shifted update (k_ms_coef -> k_ms_shift).
+struct MsCoef {
+  double2 inv_pi, beta_s, alpha_s;
+};
+
+// One queued run.
+struct MsItem {
+  int ik, kind, rep, idx;
+  long long col;  // UNIT: left-CAP column
+};
+
+struct SweepBufs {
+  int S = 0, ne = 0;
+  long long n = 0, no = 0;
+  int nblk_st = 0, nblk3 = 0, nitems = 0, nrnd = 0;
+  double2 *R = nullptr, *P0 = nullptr, *P1 = nullptr, *Q = nullptr;
+  double2 *XS = nullptr, *PS = nullptr;
+  double *sig_part = nullptr, *rho_part = nullptr;
+  Slot* slots = nullptr;
+  MsSlot* ms = nullptr;
+  MsShift* sh = nullptr;
+  MsCoef* coef = nullptr;
+  Queue* queue = nullptr;
+  MsItem* items = nullptr;
+  double* energies = nullptr;
+  double2* rnd = nullptr;
+  int *lrank = nullptr, *rrank = nullptr;
+  // capacities (elements) of the buffers above, kept between calls
+  size_t cap_vec = 0, cap_shv = 0, cap_sig = 0, cap_rho = 0, cap_slots = 0, cap_shs = 0;
+  size_t cap_items = 0, cap_ene = 0, cap_rnd = 0, cap_nz = 0;
+  void release() {
+    cudaFree(R); cudaFree(P0); cudaFree(P1); cudaFree(Q); cudaFree(XS); cudaFree(PS);
+    cudaFree(sig_part); cudaFree(rho_part); cudaFree(slots); cudaFree(ms); cudaFree(sh);
+    cudaFree(coef); cudaFree(queue); cudaFree(items); cudaFree(energies); cudaFree(rnd);
+    cudaFree(lrank); cudaFree(rrank);
+    *this = SweepBufs{};
+  }
+};
+
+void sweep_release(transec_ctx* ctx) {
+  if (ctx && ctx->sweep) {
+    ctx->sweep->release();
+    delete ctx->sweep;
+    ctx->sweep = nullptr;
+  }
+}
+
+}  // namespace transec
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// random phases: splitmix64 (Steele, Lea & Flood, OOPSLA 2014) of a counter built
+// from the seed, the run group, the kind, the vector index and the point
+// ---------------------------------------------------------------------------------
+
+__host__ __device__ inline unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+struct RandomArgs {
+  double2* rnd;  // [rep][2 kinds][smax][np]
+  int nrep, smax;
+  long long np;
+  unsigned long long seed;
+};
+
+// rnd[rep][kind][i][u] = exp(2 pi i theta), theta uniform in [0, 1) (53 bits)
+__global__ void __launch_bounds__(256) k_ms_random(const RandomArgs a) {
+  const long long total = (long long)a.nrep * 2 * a.smax * a.np;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long h = splitmix64(a.seed ^ splitmix64((unsigned long long)e));
+    const double theta = (double)(h >> 11) * 0x1.0p-53;
+    double s, c;
+    sincospi(2.0 * theta, &s, &c);
+    a.rnd[e] = make_double2(c, s);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// queue: assignment, vector initialisation, rho_0
+// ---------------------------------------------------------------------------------
+
+struct MsArgs {
+  Slot* slots;
+  MsSlot* ms;
+  MsShift* sh;
+  MsCoef* coef;
+  Queue* queue;
+  const MsItem* items;
+  const double* energies;  // ne
+  double e0;               // seed energy
+  int S, ne, nk;
+  double2* R;
+  double2* P0;
+  double2* XS;
+  double2* PS;
+  const double2* rnd;      // [rep][2][smax][np]
+  int smax;
+  long long np;            // points per random vector (largest CAP support)
+  long long n, no, nxy;
+  const int* lplanes;
+  const int* rplanes;
+  const int* lrank;        // per plane: index among the left-CAP planes, or -1
+  const int* rrank;
+  int nlp, nrp;
+  const double* gl;
+  const double* gr;
+  const double* rho_part;  // [slot][nblk3][4]
+  int nblk3;
+  const double* sig_part;  // [slot][nblk_st][2]
+  int nblk_st;
+  double tol;
+  int maxit;
+  // UNIT results: [item][shift][2] t, [item][shift] iterations and status
+  double* res_t;
+  int* res_it;
+  int* res_st;
+};
+
+// Hands queued runs to idle slots in slot order (one thread: the refill of a chunk is
+// a few slots, and the order must not depend on the launch).
+__global__ void k_ms_assign(const MsArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  Queue* q = a.queue;
+  int next = q->next;
+  for (int s = 0; s < a.S; ++s) {
+    Slot& st = a.slots[s];
+    st.init = 0;
+    if (st.status != SLOT_IDLE || next >= q->nitems) continue;
+    const MsItem it = a.items[next];
+    Slot ns{};
+    ns.status = SLOT_ACTIVE;
+    ns.item = next;
+    ns.ik = it.ik;
+    ns.e = a.e0;
+    ns.init = 1;
+    ns.j = it.kind == RUN_UNIT
+               ? (long long)a.lplanes[it.col / a.nxy] * a.nxy + it.col % a.nxy
+               : -1;
+    ns.beta = make_double2(0.0, 0.0);
+    ns.rho = make_double2(2.0, 0.0);  // <e_j, e_j> in the pairing form; k_ms_rho0 sets the rest
+    st = ns;
+    MsSlot m{};
+    m.alpha = make_double2(0.0, 0.0);
+    m.alpha_prev = make_double2(1.0, 0.0);
+    m.bnorm = 1.0;
+    m.kind = it.kind;
+    m.rep = it.rep;
+    m.idx = it.idx;
+    a.ms[s] = m;
+    ++next;
+  }
+  q->next = next;
+}
+
+// r = b on both halves, p = 0, for newly assigned slots.  grid (blocks, S)
+__global__ void __launch_bounds__(256) k_ms_init(const MsArgs a) {
+  const int slot = blockIdx.y;
+  const Slot& st = a.slots[slot];
+  if (!st.init) return;
+  const MsSlot m = a.ms[slot];
+  const double2* rl = a.rnd + (((long long)m.rep * 2 + 0) * a.smax + m.idx) * a.np;
+  const double2* rr = a.rnd + (((long long)m.rep * 2 + 1) * a.smax + m.idx) * a.np;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double2 b = make_double2(0.0, 0.0);
+    const int pl = (int)(i / a.nxy);
+    const long long w = i % a.nxy;
+    if (m.kind == RUN_UNIT) {
+      if (i == st.j) b.x = 1.0;
+    } else if (m.kind == RUN_LEFT) {
+      const int rk = a.lrank[pl];
+      if (rk >= 0) {
+        const double s = sqrt(a.gl[pl]);
+        const double2 o = rl[(long long)rk * a.nxy + w];
+        b = make_double2(s * o.x, s * o.y);
+      }
+    } else {
+      const int rk = a.rrank[pl];
+      if (rk >= 0) {
+        const double s = sqrt(a.gr[pl]);
+        const double2 o = rr[(long long)rk * a.nxy + w];
+        b = make_double2(s * o.x, s * o.y);
+      }
+    }
+    for (int h = 0; h < 2; ++h) {
+      const long long off = (long long)slot * 2 * a.n + (long long)h * a.n + i;
+      a.R[off] = b;
+      a.P0[off] = make_double2(0.0, 0.0);
+    }
+  }
+}
+
+// Per-shift vectors and scalars of newly assigned slots.  grid (blocks, ne, S)
+__global__ void __launch_bounds__(256) k_ms_init_shift(const MsArgs a) {
+  const int slot = blockIdx.z, s = blockIdx.y;
+  if (!a.slots[slot].init) return;
+  const long long base = ((long long)slot * a.ne + s) * 2 * a.no;
+  for (long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x; u < 2 * a.no;
+       u += (long long)gridDim.x * blockDim.x) {
+    a.XS[base + u] = make_double2(0.0, 0.0);
+    a.PS[base + u] = make_double2(0.0, 0.0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    MsShift z{};
+    z.pi = z.pi_prev = z.pi_next = make_double2(1.0, 0.0);
+    const double e = a.energies[s];
+    z.active = isfinite(e) ? 1 : 0;
+    z.status = isfinite(e) ? kENOCONV : kEINVAL;
+    z.conv_it = 0;
+    a.sh[(long long)slot * a.ne + s] = z;
+  }
+}
+
+// rho_0 = 2 b.b (pairing form of the two equal halves) and ||b|| of new random runs.
+// grid S, 256 threads
+__global__ void __launch_bounds__(256) k_ms_rho0(const MsArgs a) {
+  __shared__ double red[3][32];
+  const int slot = blockIdx.x;
+  Slot& st = a.slots[slot];
+  if (!st.init) return;
+  MsSlot& m = a.ms[slot];
+  if (m.kind == RUN_UNIT) return;
+  const int* planes = m.kind == RUN_LEFT ? a.lplanes : a.rplanes;
+  const long long np = (long long)(m.kind == RUN_LEFT ? a.nlp : a.nrp) * a.nxy;
+  const double2* r = a.R + (long long)slot * 2 * a.n;
+  double v[3] = {0.0, 0.0, 0.0};
+  for (long long u = threadIdx.x; u < np; u += blockDim.x) {
+    const double2 b = r[(long long)planes[u / a.nxy] * a.nxy + u % a.nxy];
+    v[0] += b.x * b.x - b.y * b.y;
+    v[1] += 2.0 * b.x * b.y;
+    v[2] += b.x * b.x + b.y * b.y;
+  }
+  block_sum<3>(v, red);
+  if (threadIdx.x == 0) {
+    st.rho = make_double2(2.0 * v[0], 2.0 * v[1]);
+    m.bnorm = sqrt(v[2]);
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// one iteration: coefficients, shifted update, convergence
+// ---------------------------------------------------------------------------------
+
+// alpha_n of the seed and pi_{n+1}, alpha_sigma, beta_sigma, 1/pi_n of every active
+// shift.  grid S, 256 threads
+__global__ void __launch_bounds__(256) k_ms_coef(const MsArgs a) {
+  __shared__ double2 s_alpha;
+  const int slot = blockIdx.x;
+  const Slot& st = a.slots[slot];
+  if (st.status != SLOT_ACTIVE) return;
+  if (threadIdx.x < 32) {
+    const double2 al = slot_alpha(a.sig_part + (size_t)slot * a.nblk_st * 2, a.nblk_st, st.rho);
+    if (threadIdx.x == 0) {
+      s_alpha = al;
+      a.ms[slot].alpha = al;
+    }
+  }
+  __syncthreads();
+  const double2 al = s_alpha;
+  const double2 bp = st.beta;                 // beta_{n-1}
+  const double2 ap = a.ms[slot].alpha_prev;   // alpha_{n-1}
+  const double2 c = cdiv(cmul(al, bp), ap);   // alpha_n beta_{n-1} / alpha_{n-1}
+  for (int s = threadIdx.x; s < a.ne; s += blockDim.x) {
+    MsShift& z = a.sh[(long long)slot * a.ne + s];
+    if (!z.active) continue;
+    const double sig = a.energies[s] - st.e;
+    const double2 t1 = cmul(make_double2(1.0 + al.x * sig, al.y * sig), z.pi);
+    const double2 t2 = cmul(c, csub(z.pi, z.pi_prev));
+    const double2 pn = cadd(t1, t2);
+    if (!(isfinite(pn.x) && isfinite(pn.y)) || (pn.x == 0.0 && pn.y == 0.0)) {
+      z.active = 0;
+      z.status = kEBREAKDOWN;
+      z.conv_it = st.it + 1;
+      continue;
+    }
+    z.pi_next = pn;
+    MsCoef co;
+    co.alpha_s = cdiv(cmul(al, z.pi), pn);
+    co.inv_pi = cdiv(make_double2(1.0, 0.0), z.pi);
+    const double2 ratio = cdiv(z.pi_prev, z.pi);
+    co.beta_s = cmul(cmul(ratio, ratio), bp);
+    a.coef[(long long)slot * a.ne + s] = co;
+  }
+}
+
+// p_sigma = r_n / pi_n + beta_sigma p_sigma, x_sigma += alpha_sigma p_sigma on the kept
+// planes, both halves, active shifts.  grid (ceil(no / 256), ne, S)
+__global__ void __launch_bounds__(256) k_ms_shift(const MsArgs a) {
+  const int slot = blockIdx.z, s = blockIdx.y;
+  if (a.slots[slot].status != SLOT_ACTIVE) return;
+  const long long zs = (long long)slot * a.ne + s;
+  if (!a.sh[zs].active) return;
+  const MsCoef co = a.coef[zs];
+  const int kind = a.ms[slot].kind;
+  const int* planes = kind == RUN_RIGHT ? a.lplanes : a.rplanes;
+  const long long nro = (long long)(kind == RUN_RIGHT ? a.nlp : a.nrp) * a.nxy;
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= nro) return;
+  const long long pt = (long long)planes[u / a.nxy] * a.nxy + u % a.nxy;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double2 rv = a.R[(long long)slot * 2 * a.n + (long long)h * a.n + pt];
+    const long long off = (zs * 2 + h) * a.no + u;
+    double2 pv = a.PS[off];
+    pv = cadd(cmul(rv, co.inv_pi), cmul(co.beta_s, pv));
+    a.PS[off] = pv;
+    a.XS[off] = cadd(a.XS[off], cmul(co.alpha_s, pv));
+  }
+}
+
+// Seed residual norms and rho_{n+1}, shift convergence (residual of the shift =
+// max(||r||, ||r~||) / |pi_{n+1}|), maxit and breakdown, beta_n.  grid S, 256 threads
+__global__ void __launch_bounds__(256) k_ms_scalars(const MsArgs a) {
+  __shared__ double s_v[4];
+  __shared__ int s_live[8];
+  const int slot = blockIdx.x;
+  Slot& st = a.slots[slot];
+  if (st.status != SLOT_ACTIVE) return;
+  if (threadIdx.x < 32) {
+    double v[4] = {0, 0, 0, 0};
+    const double* rp = a.rho_part + (size_t)slot * a.nblk3 * 4;
+    for (int b = threadIdx.x; b < a.nblk3; b += 32)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] += rp[4 * b + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = warp_sum(v[k]);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 4; ++k) s_v[k] = v[k];
+  }
+  __syncthreads();
+  const double2 rho_new = make_double2(s_v[0], s_v[1]);
+  const double rn = sqrt(fmax(s_v[2], s_v[3]));
+  const int it = st.it + 1;
+  const double thresh = a.tol * a.ms[slot].bnorm;
+  const bool brk = !(isfinite(rho_new.x) && isfinite(rho_new.y)) ||
+                   (rho_new.x == 0.0 && rho_new.y == 0.0) || !isfinite(rn);
+  int live = 0;
+  for (int s = threadIdx.x; s < a.ne; s += blockDim.x) {
+    MsShift& z = a.sh[(long long)slot * a.ne + s];
+    if (!z.active) continue;
+    z.pi_prev = z.pi;
+    z.pi = z.pi_next;
+    const double res = rn / hypot(z.pi.x, z.pi.y);
+    if (isfinite(res) && res <= thresh) {
+      z.active = 0;
+      z.status = kOK;
+      z.conv_it = it;
+    } else if (brk || !isfinite(res)) {
+      z.active = 0;
+      z.status = kEBREAKDOWN;
+      z.conv_it = it;
+    } else if (it >= a.maxit) {
+      z.active = 0;
+      z.status = kENOCONV;
+      z.conv_it = it;
+    } else {
+      ++live;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) live += __shfl_down_sync(0xffffffffu, live, o);
+  if ((threadIdx.x & 31) == 0) s_live[threadIdx.x >> 5] = live;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_live[w];
+    st.it = it;
+    st.res = rn;
+    if (tot == 0) {
+      st.status = SLOT_DONE;
+      st.result = kOK;
+    } else {
+      st.beta = cdiv(rho_new, st.rho);
+      st.rho = rho_new;
+      a.ms[slot].alpha_prev = a.ms[slot].alpha;
+    }
+  }
+}
+
+// UNIT runs that finished: t_j = 4 Gamma_L(j) sum_R Gamma_R |x_sigma|^2 per shift and
+// half.  grid (ne, S), 256 threads
+__global__ void __launch_bounds__(256) k_ms_trace(const MsArgs a) {
+  __shared__ double red[2][32];
+  const int s = blockIdx.x, slot = blockIdx.y;
+  const Slot& st = a.slots[slot];
+  if (st.status != SLOT_DONE || a.ms[slot].kind != RUN_UNIT) return;
+  const long long zs = (long long)slot * a.ne + s;
+  const long long nro = (long long)a.nrp * a.nxy;
+  double v[2] = {0.0, 0.0};
+  for (int h = 0; h < 2; ++h) {
+    const double2* x = a.XS + (zs * 2 + h) * a.no;
+    double acc = 0.0;
+    for (long long u = threadIdx.x; u < nro; u += blockDim.x) {
+      const double2 xv = x[u];
+      acc += a.gr[a.rplanes[u / a.nxy]] * (xv.x * xv.x + xv.y * xv.y);
+    }
+    v[h] = acc;
+  }
+  block_sum<2>(v, red);
+  if (threadIdx.x == 0) {
+    const MsShift z = a.sh[zs];
+    const double glj = a.gl[st.j / a.nxy];
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    const long long o = (long long)st.item * a.ne + s;
+    a.res_t[2 * o] = z.status == kOK ? 4.0 * glj * v[0] : nan;
+    a.res_t[2 * o + 1] = z.status == kOK ? 4.0 * glj * v[1] : nan;
+    a.res_it[o] = z.conv_it;
+    a.res_st[o] = z.status;
+  }
+}
+
+// Finished runs release their slots (in slot order) and count as harvested.
+__global__ void k_ms_release(const MsArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int h = 0;
+  for (int s = 0; s < a.S; ++s) {
+    Slot& st = a.slots[s];
+    if (st.status != SLOT_DONE) continue;
+    st.status = SLOT_IDLE;
+    st.item = -1;
+    ++h;
+  }
+  a.queue->harvested += h;
+}
+
+// ---------------------------------------------------------------------------------
+// two-sided sketch reduction: T(E, +-k) per shift from the LEFT / RIGHT runs
+// ---------------------------------------------------------------------------------
+
+struct GnArgs {
+  double2* XS;             // [slot][ne][2][no]; the LEFT runs' kept planes are
+                           // orthogonalised in place
+  const MsShift* sh;
+  const int* run_slot;     // [rep][sl + sr]: slots of the LEFT runs, then the RIGHT runs
+  const double2* rnd;      // [rep][2][smax][np]
+  int smax;
+  long long np, no, nxy;
+  int ne, sl, sr;
+  const int* lplanes;
+  const int* rplanes;
+  int nlp, nrp;
+  const double* gl;
+  const double* gr;
+  double* T;               // [rep][ne][2] (T(E, k), T(E, -k))
+  int* rank;               // [rep][ne][2]
+  int* status;             // [rep][ne][2]
+  double drop;             // relative norm below which a column of Y adds no direction
+};
+
+constexpr int kGnMaxL = 32, kGnMaxR = 64;
+
+// Block sum of up to 2*kGnChunk doubles per thread into s_out (valid after return).
+template <int NV>
+__device__ inline void gn_block_sum(double (&v)[NV], double* s_out, double (*red)[32]) {
+  block_sum<NV>(v, red);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s_out[k] = v[k];
+  __syncthreads();
+}
+
+constexpr int kGnChunk = 8;
+
+// grid (ne, nrep, 2 signs), 256 threads, dynamic shared memory for K and G_b
+__global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
+  extern __shared__ __align__(16) unsigned char gn_smem[];
+  __shared__ double red[2 * kGnChunk][32];
+  __shared__ double s_red[2 * kGnChunk];
+  __shared__ double2 s_d[kGnMaxL];
+  __shared__ int s_keep[kGnMaxL];
+  __shared__ int s_status;
+  __shared__ double s_nrm0;
+  __shared__ double2 s_v[kGnMaxR];
+  __shared__ int s_cols[kGnMaxL];
+  const int s = blockIdx.x, rep = blockIdx.y, sign = blockIdx.z;
+  const int hY = sign, hW = 1 - sign;  // +k: primal of LEFT, shadow of RIGHT; -k: swapped
+  const int sl = a.sl, sr = a.sr;
+  double2* K = reinterpret_cast<double2*>(gn_smem);   // [sr][sl]
+  double2* Gb = K + kGnMaxR * kGnMaxL;                 // [sr][sr]
+  const int* rs = a.run_slot + (long long)rep * (sl + sr);
+  const long long o_out = ((long long)rep * a.ne + s) * 2 + sign;
+  if (threadIdx.x == 0) {
+    int w = kOK;
+    for (int c = 0; c < sl + sr; ++c) {
+      const int st = a.sh[(long long)rs[c] * a.ne + s].status;
+      if (st != kOK && w == kOK) w = st;
+    }
+    s_status = w;
+  }
+  __syncthreads();
+  if (s_status != kOK) {
+    if (threadIdx.x == 0) {
+      a.T[o_out] = __longlong_as_double(0x7ff8000000000000LL);
+      a.rank[o_out] = 0;
+      a.status[o_out] = s_status;
+    }
+    return;
+  }
+  const long long nR = (long long)a.nrp * a.nxy, nL = (long long)a.nlp * a.nxy;
+  auto ycol = [&](int c) { return a.XS + (((long long)rs[c] * a.ne + s) * 2 + hY) * a.no; };
+  auto wcol = [&](int i) { return a.XS + (((long long)rs[sl + i] * a.ne + s) * 2 + hW) * a.no; };
+  // Y = Gamma_R^1/2 x on the right-CAP planes, in place
+  for (int c = 0; c < sl; ++c) {
+    double2* y = ycol(c);
+    for (long long u = threadIdx.x; u < nR; u += blockDim.x) {
+      const double g = sqrt(a.gr[a.rplanes[u / a.nxy]]);
+      y[u] = make_double2(g * y[u].x, g * y[u].y);
+    }
+  }
+  __syncthreads();
+  // Q = orth(Y): classical Gram-Schmidt, twice per column; a column whose remaining
+  // norm is below drop x its own norm lies in the span already and is skipped
+  for (int c = 0; c < sl; ++c) {
+    double2* y = ycol(c);
+    {
+      double v[1] = {0.0};
+      for (long long u = threadIdx.x; u < nR; u += blockDim.x) v[0] += y[u].x * y[u].x + y[u].y * y[u].y;
+      gn_block_sum<1>(v, s_red, red);
+      if (threadIdx.x == 0) s_nrm0 = sqrt(s_red[0]);
+      __syncthreads();
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j0 = 0; j0 < c; j0 += kGnChunk) {
+        double v[2 * kGnChunk];
+#pragma unroll
+        for (int k = 0; k < 2 * kGnChunk; ++k) v[k] = 0.0;
+        for (long long u = threadIdx.x; u < nR; u += blockDim.x) {
+          const double2 yv = y[u];
+#pragma unroll
+          for (int k = 0; k < kGnChunk; ++k) {
+            const int j = j0 + k;
+            if (j < c && s_keep[j]) {
+              const double2 qv = ycol(j)[u];  // <q_j, y> = sum conj(q) y
+              v[2 * k] += qv.x * yv.x + qv.y * yv.y;
+              v[2 * k + 1] += qv.x * yv.y - qv.y * yv.x;
+            }
+          }
+        }
+        gn_block_sum<2 * kGnChunk>(v, s_red, red);
+        if (threadIdx.x < kGnChunk && j0 + threadIdx.x < c)
+          s_d[j0 + threadIdx.x] = make_double2(s_red[2 * threadIdx.x], s_red[2 * threadIdx.x + 1]);
+        __syncthreads();
+      }
+      for (long long u = threadIdx.x; u < nR; u += blockDim.x) {
+        double2 yv = y[u];
+        for (int j = 0; j < c; ++j)
+          if (s_keep[j]) yv = csub(yv, cmul(s_d[j], ycol(j)[u]));
+        y[u] = yv;
+      }
+      __syncthreads();
+    }
+    double v[1] = {0.0};
+    for (long long u = threadIdx.x; u < nR; u += blockDim.x) v[0] += y[u].x * y[u].x + y[u].y * y[u].y;
+    gn_block_sum<1>(v, s_red, red);
+    const double nrm = sqrt(s_red[0]);
+    const int keep = nrm > a.drop * s_nrm0 && nrm > 0.0;
+    if (keep) {
+      const double inv = 1.0 / nrm;
+      for (long long u = threadIdx.x; u < nR; u += blockDim.x) y[u] = make_double2(inv * y[u].x, inv * y[u].y);
+    }
+    if (threadIdx.x == 0) s_keep[c] = keep;
+    __syncthreads();
+  }
+  // K[i][c] = psi_i^T q_c (bilinear) for the kept columns
+  const double2* psi = a.rnd + ((long long)rep * 2 + 1) * a.smax * a.np;
+  for (int i = 0; i < sr; ++i) {
+    const double2* pv = psi + (long long)i * a.np;
+    for (int j0 = 0; j0 < sl; j0 += kGnChunk) {
+      double v[2 * kGnChunk];
+#pragma unroll
+      for (int k = 0; k < 2 * kGnChunk; ++k) v[k] = 0.0;
+      for (long long u = threadIdx.x; u < nR; u += blockDim.x) {
+        const double2 p = pv[u];
+#pragma unroll
+        for (int k = 0; k < kGnChunk; ++k) {
+          const int j = j0 + k;
+          if (j < sl && s_keep[j]) {
+            const double2 q = ycol(j)[u];
+            v[2 * k] += p.x * q.x - p.y * q.y;
+            v[2 * k + 1] += p.x * q.y + p.y * q.x;
+          }
+        }
+      }
+      gn_block_sum<2 * kGnChunk>(v, s_red, red);
+      if (threadIdx.x < kGnChunk && j0 + threadIdx.x < sl)
+        K[i * kGnMaxL + j0 + threadIdx.x] = make_double2(s_red[2 * threadIdx.x], s_red[2 * threadIdx.x + 1]);
+      __syncthreads();
+    }
+  }
+  // G_b[i][j] = sum_v w_i(v) conj(w_j(v)), w_i = Gamma_L^1/2 (kept planes of RIGHT run i)
+  for (int i = 0; i < sr; ++i) {
+    const double2* wi = wcol(i);
+    for (int j0 = i; j0 < sr; j0 += kGnChunk) {
+      double v[2 * kGnChunk];
+#pragma unroll
+      for (int k = 0; k < 2 * kGnChunk; ++k) v[k] = 0.0;
+      for (long long u = threadIdx.x; u < nL; u += blockDim.x) {
+        const double g = a.gl[a.lplanes[u / a.nxy]];
+        const double2 x = wi[u];
+#pragma unroll
+        for (int k = 0; k < kGnChunk; ++k) {
+          const int j = j0 + k;
+          if (j < sr) {
+            const double2 w = wcol(j)[u];
+            v[2 * k] += g * (x.x * w.x + x.y * w.y);
+            v[2 * k + 1] += g * (x.y * w.x - x.x * w.y);
+          }
+        }
+      }
+      gn_block_sum<2 * kGnChunk>(v, s_red, red);
+      if (threadIdx.x < kGnChunk && j0 + threadIdx.x < sr) {
+        const int j = j0 + threadIdx.x;
+        const double2 g = make_double2(s_red[2 * threadIdx.x], s_red[2 * threadIdx.x + 1]);
+        Gb[i * kGnMaxR + j] = g;
+        Gb[j * kGnMaxR + i] = make_double2(g.x, -g.y);
+      }
+      __syncthreads();
+    }
+  }
+  // small dense part (one thread, all in shared memory): Householder QR of K on the
+  // kept columns (R_K in place in K), Z = Q_K^H G_b Q_K (in place in G_b), then
+  // T = 4 trace(R_K^-1 Z R_K^-H)
+  if (threadIdx.x == 0) {
+    double2* v = s_v;
+    int* cols = s_cols;
+    int r = 0;
+    for (int c = 0; c < sl; ++c)
+      if (s_keep[c]) cols[r++] = c;
+    const int m = sr;
+    for (int t = 0; t < r; ++t) {
+      // reflector H = I - 2 v v^H taking column cols[t] (rows t..m-1) to alpha e_t
+      double nx = 0.0;
+      for (int i = t; i < m; ++i) {
+        const double2 k = K[i * kGnMaxL + cols[t]];
+        nx += k.x * k.x + k.y * k.y;
+      }
+      nx = sqrt(nx);
+      const double2 x0 = K[t * kGnMaxL + cols[t]];
+      const double ax0 = hypot(x0.x, x0.y);
+      const double2 ph = ax0 > 0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+      const double2 alpha = make_double2(-ph.x * nx, -ph.y * nx);  // -e^{i arg x0} ||x||
+      for (int i = t; i < m; ++i) v[i] = K[i * kGnMaxL + cols[t]];
+      v[t] = csub(v[t], alpha);
+      double nv = 0.0;
+      for (int i = t; i < m; ++i) nv += v[i].x * v[i].x + v[i].y * v[i].y;
+      nv = sqrt(nv);
+      if (nv > 0.0)
+        for (int i = t; i < m; ++i) v[i] = make_double2(v[i].x / nv, v[i].y / nv);
+      else
+        for (int i = t; i < m; ++i) v[i] = make_double2(0.0, 0.0);
+      for (int tt = t; tt < r; ++tt) {  // K <- H K on the kept columns
+        double2 d = make_double2(0.0, 0.0);
+        for (int i = t; i < m; ++i) {
+          const double2 k = K[i * kGnMaxL + cols[tt]];
+          d = cadd(d, make_double2(v[i].x * k.x + v[i].y * k.y, v[i].x * k.y - v[i].y * k.x));
+        }
+        for (int i = t; i < m; ++i) {
+          double2& k = K[i * kGnMaxL + cols[tt]];
+          k = csub(k, cmul(make_double2(2.0 * v[i].x, 2.0 * v[i].y), d));
+        }
+      }
+      for (int j = 0; j < m; ++j) {  // G_b <- H G_b: rows t..m-1
+        double2 d = make_double2(0.0, 0.0);
+        for (int i = t; i < m; ++i) {
+          const double2 g = Gb[i * kGnMaxR + j];
+          d = cadd(d, make_double2(v[i].x * g.x + v[i].y * g.y, v[i].x * g.y - v[i].y * g.x));
+        }
+        for (int i = t; i < m; ++i)
+          Gb[i * kGnMaxR + j] = csub(Gb[i * kGnMaxR + j], cmul(make_double2(2.0 * v[i].x, 2.0 * v[i].y), d));
+      }
+      for (int i = 0; i < m; ++i) {  // G_b <- G_b H = G_b - 2 (G_b v) v^H: columns t..m-1
+        double2 d = make_double2(0.0, 0.0);
+        for (int j = t; j < m; ++j) d = cadd(d, cmul(Gb[i * kGnMaxR + j], v[j]));
+        for (int j = t; j < m; ++j)
+          Gb[i * kGnMaxR + j] =
+              csub(Gb[i * kGnMaxR + j], cmul(make_double2(2.0 * d.x, 2.0 * d.y), make_double2(v[j].x, -v[j].y)));
+      }
+    }
+    // R_K[i][j] = K[i][cols[j]] (i <= j < r).  A1 = R^-1 Z by back substitution, in
+    // place over Z = G_b[0:r][0:r]
+    bool bad = false;
+    for (int i = 0; i < r; ++i) {
+      const double2 d = K[i * kGnMaxL + cols[i]];
+      if (!(d.x != 0.0 || d.y != 0.0)) bad = true;
+    }
+    double tr = 0.0;
+    if (!bad) {
+      for (int j = 0; j < r; ++j)
+        for (int i = r - 1; i >= 0; --i) {
+          double2 acc = Gb[i * kGnMaxR + j];
+          for (int l = i + 1; l < r; ++l) acc = csub(acc, cmul(K[i * kGnMaxL + cols[l]], Gb[l * kGnMaxR + j]));
+          Gb[i * kGnMaxR + j] = cdiv(acc, K[i * kGnMaxL + cols[i]]);
+        }
+      // diagonal of R^-1 A1^H (its real part equals that of M2 = A1 R^-H, its conjugate
+      // transpose): column j of A1^H is conj(row j of A1)
+      for (int j = 0; j < r; ++j) {
+        double2* col = v;
+        for (int i = r - 1; i >= 0; --i) {
+          const double2 aji = Gb[j * kGnMaxR + i];
+          double2 acc = make_double2(aji.x, -aji.y);
+          for (int l = i + 1; l < r; ++l) acc = csub(acc, cmul(K[i * kGnMaxL + cols[l]], col[l]));
+          col[i] = cdiv(acc, K[i * kGnMaxL + cols[i]]);
+        }
+        tr += col[j].x;
+      }
+    }
+    a.T[o_out] = bad ? __longlong_as_double(0x7ff8000000000000LL) : 4.0 * tr;
+    a.rank[o_out] = r;
+    a.status[o_out] = bad ? kEBREAKDOWN : kOK;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------------
+
+struct DevScope {
+  int prev = -1;
+  explicit DevScope(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(d);
+  }
+  ~DevScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int ms_fail(transec_ctx* ctx, int code, const std::string& msg) {
+  ctx->err = msg;
+  return code;
+}
+
+int ms_severity(int code) {
+  switch (code) {
+    case TRANSEC_OK: return 0;
+    case TRANSEC_ENOCONV: return 1;
+    case TRANSEC_EBREAKDOWN: return 2;
+    case TRANSEC_ETIMEOUT: return 3;
+    default: return 4;
+  }
+}
+
+#define MS_CK(call)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      cudaGetLastError();                                                               \
+      return ms_fail(ctx, e_ == cudaErrorMemoryAllocation ? TRANSEC_ENOMEM : TRANSEC_ECUDA, \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    }                                                                                   \
+  } while (0)
+
+// (Re)allocate p to hold `need` elements unless its capacity `have` suffices.
+template <typename P>
+cudaError_t grow(P*& p, size_t have, size_t need) {
+  if (have >= need && p) return cudaSuccess;
+  cudaFree(p);
+  p = nullptr;
+  return cudaMalloc(&p, std::max<size_t>(need, 1) * sizeof(P));
+}
+
+// One solve of the multi-shift engine: items run to completion (every shift converged
+// or stopped), per-shift vectors left in the buffers for the reductions.
+int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vector<double>& energies,
+              double e0, int S, int nrep, int smax, unsigned long long seed, double** d_res_t,
+              int** d_res_it, int** d_res_st) {
+  SweepBufs& B = *ctx->sweep;
+  const Geometry& g = ctx->g;
+  const int ne = (int)energies.size();
+  const int nitems = (int)items.size();
+  const long long n = g.n, nxy = g.nxy;
+  const int nlp = (int)ctx->lplanes.size(), nrp = (int)ctx->rplanes.size();
+  const long long no = (long long)std::max(nlp, nrp) * nxy;
+  const TileShape ts = choose_tiles(g, 2, sizeof(double2), StencilMax<double>::threads, ctx->opts.tile_y,
+                                    ctx->opts.slab);
+  const int nblk_st = ts.ntx * ts.nty * ts.nslab;
+  const int nblk3 = (int)std::min(1024LL, (n + 256 * 8 - 1) / (256 * 8));
+  const long long np = no;
+  const size_t need_vec = (size_t)S * 2 * n, need_shv = (size_t)S * ne * 2 * no;
+  const size_t need_rnd = (size_t)std::max(1, nrep) * 2 * std::max(1, smax) * np;
+  MS_CK(grow(B.R, B.cap_vec, need_vec));
+  MS_CK(grow(B.P0, B.cap_vec, need_vec));
+  MS_CK(grow(B.P1, B.cap_vec, need_vec));
+  MS_CK(grow(B.Q, B.cap_vec, need_vec));
+  B.cap_vec = std::max(B.cap_vec, need_vec);
+  MS_CK(grow(B.XS, B.cap_shv, need_shv));
+  MS_CK(grow(B.PS, B.cap_shv, need_shv));
+  B.cap_shv = std::max(B.cap_shv, need_shv);
+  MS_CK(grow(B.sig_part, B.cap_sig, (size_t)S * nblk_st * 2));
+  B.cap_sig = std::max(B.cap_sig, (size_t)S * nblk_st * 2);
+  MS_CK(grow(B.rho_part, B.cap_rho, (size_t)S * nblk3 * 4));
+  B.cap_rho = std::max(B.cap_rho, (size_t)S * nblk3 * 4);
+  MS_CK(grow(B.slots, B.cap_slots, (size_t)S));
+  MS_CK(grow(B.ms, B.cap_slots, (size_t)S));
+  B.cap_slots = std::max(B.cap_slots, (size_t)S);
+  MS_CK(grow(B.sh, B.cap_shs, (size_t)S * ne));
+  MS_CK(grow(B.coef, B.cap_shs, (size_t)S * ne));
+  B.cap_shs = std::max(B.cap_shs, (size_t)S * ne);
+  MS_CK(grow(B.items, B.cap_items, (size_t)nitems));
+  B.cap_items = std::max(B.cap_items, (size_t)nitems);
+  MS_CK(grow(B.energies, B.cap_ene, (size_t)ne));
+  B.cap_ene = std::max(B.cap_ene, (size_t)ne);
+  MS_CK(grow(B.rnd, B.cap_rnd, need_rnd));
+  B.cap_rnd = std::max(B.cap_rnd, need_rnd);
+  MS_CK(grow(B.lrank, B.cap_nz, (size_t)g.nz));
+  MS_CK(grow(B.rrank, B.cap_nz, (size_t)g.nz));
+  B.cap_nz = std::max(B.cap_nz, (size_t)g.nz);
+  if (!B.queue) MS_CK(cudaMalloc(&B.queue, sizeof(Queue)));
+  B.S = S; B.ne = ne; B.n = n; B.no = no; B.nblk_st = nblk_st; B.nblk3 = nblk3; B.nitems = nitems;
+  B.nrnd = nrep;
+  cudaStream_t st = ctx->s;
+  std::vector<int> lr(g.nz, -1), rr(g.nz, -1);
+  for (int i = 0; i < nlp; ++i) lr[ctx->lplanes[i]] = i;
+  for (int i = 0; i < nrp; ++i) rr[ctx->rplanes[i]] = i;
+  MS_CK(cudaMemcpyAsync(B.lrank, lr.data(), g.nz * sizeof(int), cudaMemcpyHostToDevice, st));
+  MS_CK(cudaMemcpyAsync(B.rrank, rr.data(), g.nz * sizeof(int), cudaMemcpyHostToDevice, st));
+  MS_CK(cudaMemcpyAsync(B.items, items.data(), nitems * sizeof(MsItem), cudaMemcpyHostToDevice, st));
+  MS_CK(cudaMemcpyAsync(B.energies, energies.data(), ne * sizeof(double), cudaMemcpyHostToDevice, st));
+  Queue q0{};
+  q0.nitems = nitems;
+  MS_CK(cudaMemcpyAsync(B.queue, &q0, sizeof(Queue), cudaMemcpyHostToDevice, st));
+  MS_CK(cudaMemsetAsync(B.slots, 0, (size_t)S * sizeof(Slot), st));
+  if (nrep > 0) {
+    RandomArgs ra{B.rnd, nrep, smax, np, seed};
+    k_ms_random<<<1024, 256, 0, st>>>(ra);
+    ctx->launches += 1;
+  }
+  // results of UNIT runs
+  double* res_t = nullptr;
+  int *res_it = nullptr, *res_st = nullptr;
+  MS_CK(cudaMalloc(&res_t, (size_t)std::max(1, nitems) * ne * 2 * sizeof(double)));
+  MS_CK(cudaMalloc(&res_it, (size_t)std::max(1, nitems) * ne * sizeof(int)));
+  MS_CK(cudaMalloc(&res_st, (size_t)std::max(1, nitems) * ne * sizeof(int)));
+  *d_res_t = res_t;
+  *d_res_it = res_it;
+  *d_res_st = res_st;
+
+  MsArgs a{};
+  a.slots = B.slots; a.ms = B.ms; a.sh = B.sh; a.coef = B.coef; a.queue = B.queue; a.items = B.items;
+  a.energies = B.energies; a.e0 = e0; a.S = S; a.ne = ne; a.nk = ctx->nk;
+  a.R = B.R; a.P0 = B.P0; a.XS = B.XS; a.PS = B.PS; a.rnd = B.rnd; a.smax = smax; a.np = np;
+  a.n = n; a.no = no; a.nxy = nxy; a.lplanes = ctx->d_lplanes; a.rplanes = ctx->d_rplanes;
+  a.lrank = B.lrank; a.rrank = B.rrank; a.nlp = nlp; a.nrp = nrp; a.gl = ctx->d_gl; a.gr = ctx->d_gr;
+  a.rho_part = B.rho_part; a.nblk3 = nblk3; a.sig_part = B.sig_part; a.nblk_st = nblk_st;
+  a.tol = ctx->opts.tol; a.maxit = ctx->opts.maxit;
+  a.res_t = res_t; a.res_it = res_it; a.res_st = res_st;
+
+  MS_CK(prepare_stencil<double>(g.R, ts.smem));
+  StencilArgs<double> sa{};
+  sa.r = B.R; sa.q = B.Q; sa.part = B.sig_part; sa.slots = B.slots; sa.phase = ctx->d_phase;
+  sa.v = ctx->d_v; sa.gam = ctx->d_gam; sa.g = g; sa.H = 2; sa.TX = ts.TX; sa.TY = ts.TY; sa.D = ts.D;
+  sa.ntx = ts.ntx; sa.conj = 0; sa.slot_stride = 2 * n; sa.insts = nullptr; sa.tile_idx = 0;
+  const dim3 sgrid((unsigned)(ts.ntx * ts.nty), (unsigned)ts.nslab, (unsigned)S);
+  UpdateArgs<double> ua{};
+  ua.x = nullptr; ua.r = B.R; ua.q = B.Q; ua.sig_part = B.sig_part; ua.sig_nblk = nblk_st;
+  ua.rho_part = B.rho_part; ua.slots = B.slots; ua.n = n; ua.slot_stride = 2 * n; ua.H = 2;
+  ua.insts = nullptr;
+  const dim3 ugrid((unsigned)nblk3, (unsigned)S);
+  const dim3 shgrid((unsigned)((no + 255) / 256), (unsigned)ne, (unsigned)S);
+  const dim3 igrid((unsigned)std::min<long long>((n + 255) / 256, 1024), (unsigned)S);
+  const dim3 isgrid((unsigned)std::min<long long>((2 * no + 255) / 256, 256), (unsigned)ne, (unsigned)S);
+
+  k_ms_assign<<<1, 32, 0, st>>>(a);
+  k_ms_init<<<igrid, 256, 0, st>>>(a);
+  k_ms_init_shift<<<isgrid, 256, 0, st>>>(a);
+  k_ms_rho0<<<S, 256, 0, st>>>(a);
+  MS_CK(cudaGetLastError());
+  ctx->launches += 4;
+
+  const int C = ctx->opts.chunk;
+  const bool prof = ctx->opts.profile != 0;
+  if (prof) {
+    while ((int)ctx->prof_ev.size() < 4 * C) {
+      cudaEvent_t e;
+      MS_CK(cudaEventCreate(&e));
+      ctx->prof_ev.push_back(e);
+    }
+  }
+  const bool device_loop = !prof && !ctx->opts.host_loop;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle loop{};
+  if (device_loop) {
+    MS_CK(cudaGraphCreate(&graph, 0));
+    cudaError_t eh = cudaGraphConditionalHandleCreate(&loop, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (eh == cudaSuccess) eh = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (eh == cudaSuccess)
+      eh = cudaStreamBeginCaptureToGraph(st, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+    if (eh != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return ms_fail(ctx, TRANSEC_ECUDA, std::string("device loop set-up: ") + cudaGetErrorString(eh));
+    }
+  } else {
+    MS_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  }
+  for (int i = 0; i < C; ++i) {
+    sa.p_in = (i % 2 == 0) ? B.P0 : B.P1;
+    sa.p_out = (i % 2 == 0) ? B.P1 : B.P0;
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 0], st, cudaEventRecordExternal);
+    launch_stencil<double>(g.R, sgrid, ts.threads, ts.smem, st, sa);
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 1], st, cudaEventRecordExternal);
+    k_ms_coef<<<S, 256, 0, st>>>(a);
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 2], st, cudaEventRecordExternal);
+    k_ms_shift<<<shgrid, 256, 0, st>>>(a);
+    if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 3], st, cudaEventRecordExternal);
+    ua.p = sa.p_out;
+    k_update<double><<<ugrid, 256, 0, st>>>(ua);
+    k_ms_scalars<<<S, 256, 0, st>>>(a);
+  }
+  k_ms_trace<<<dim3((unsigned)ne, (unsigned)S), 256, 0, st>>>(a);
+  k_ms_release<<<1, 32, 0, st>>>(a);
+  k_ms_assign<<<1, 32, 0, st>>>(a);
+  k_ms_init<<<igrid, 256, 0, st>>>(a);
+  k_ms_init_shift<<<isgrid, 256, 0, st>>>(a);
+  k_ms_rho0<<<S, 256, 0, st>>>(a);
+  if (device_loop) {
+    k_continue<<<1, 1, 0, st>>>(loop, B.queue);
+  } else {
+    cudaMemcpyAsync(ctx->h_harvest, &B.queue->harvested, sizeof(int), cudaMemcpyDeviceToHost, st);
+  }
+  {
+    cudaGraph_t captured = nullptr;
+    cudaError_t e1 = cudaStreamEndCapture(st, &captured);
+    if (!device_loop) graph = captured;
+    if (e1 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return ms_fail(ctx, TRANSEC_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e1));
+    }
+  }
+  {
+    cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+    if (e2 != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return ms_fail(ctx, TRANSEC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+    }
+  }
+  const long long per_chunk = 5LL * C + 6 + (device_loop ? 1 : 0);
+  const long long max_chunks =
+      ((long long)nitems / std::max(1, S) + 2) * ((long long)ctx->opts.maxit / C + 2) + 16;
+  const int per_launch = 4096;
+  long long chunks = 0;
+  int rcode = TRANSEC_OK;
+  *ctx->h_harvest = 0;
+  while (true) {
+    cudaError_t e3 = cudaSuccess;
+    if (device_loop) {
+      const int lim = (int)std::min<long long>(chunks + per_launch, 1LL << 30);
+      e3 = cudaMemcpyAsync(&B.queue->limit, &lim, sizeof(int), cudaMemcpyHostToDevice, st);
+      if (e3 == cudaSuccess) e3 = cudaGraphLaunch(exec, st);
+      Queue qh{};
+      if (e3 == cudaSuccess) e3 = cudaMemcpyAsync(&qh, B.queue, sizeof(Queue), cudaMemcpyDeviceToHost, st);
+      if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(st);
+      if (e3 == cudaSuccess) {
+        chunks = qh.chunks;
+        *ctx->h_harvest = qh.harvested;
+      }
+    } else {
+      e3 = cudaGraphLaunch(exec, st);
+      if (e3 == cudaSuccess) e3 = cudaStreamSynchronize(st);
+      if (e3 == cudaSuccess) ++chunks;
+    }
+    if (e3 != cudaSuccess) {
+      cudaGetLastError();
+      rcode = ms_fail(ctx, TRANSEC_ECUDA, std::string("multi-shift chunk: ") + cudaGetErrorString(e3));
+      break;
+    }
+    if (prof) {
+      for (int i = 0; i < C; ++i) {
+        float t0 = 0.f, t1 = 0.f;
+        if (cudaEventElapsedTime(&t0, ctx->prof_ev[4 * i], ctx->prof_ev[4 * i + 1]) == cudaSuccess) {
+          ctx->sweep_stencil_ms += t0;
+          ctx->sweep_stencil_launches += 1;
+        }
+        if (cudaEventElapsedTime(&t1, ctx->prof_ev[4 * i + 2], ctx->prof_ev[4 * i + 3]) == cudaSuccess) {
+          ctx->sweep_shift_ms += t1;
+          ctx->sweep_shift_launches += 1;
+        }
+      }
+      cudaGetLastError();
+    }
+    if (*ctx->h_harvest >= nitems) break;
+    if (chunks > max_chunks) {
+      rcode = ms_fail(ctx, TRANSEC_ETIMEOUT, "multi-shift solve did not drain its queue within the iteration bound");
+      break;
+    }
+  }
+  ctx->launches += chunks * per_chunk;
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  // work counters: seed iterations per run and shifted point updates
+  if (rcode == TRANSEC_OK) {
+    std::vector<MsShift> hsh((size_t)S * ne);
+    std::vector<Slot> hsl(S);
+    // the per-run iteration count is the largest stop iteration of its shifts; runs
+    // left in slots (the sketch keeps them) are read here, UNIT runs from the results
+    if (cudaMemcpy(hsh.data(), B.sh, hsh.size() * sizeof(MsShift), cudaMemcpyDeviceToHost) == cudaSuccess) {
+      for (int s2 = 0; s2 < S; ++s2) {
+        int mx = 0;
+        for (int e = 0; e < ne; ++e) {
+          mx = std::max(mx, hsh[(size_t)s2 * ne + e].conv_it);
+          ctx->sweep_shift_points += (long long)hsh[(size_t)s2 * ne + e].conv_it * 2 * (long long)std::max(nlp, nrp) * nxy;
+        }
+        ctx->sweep_iters += mx;
+      }
+    }
+    cudaGetLastError();
+  }
+  return rcode;
+}
+
+}  // namespace
+
+extern "C" {
+
+int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, int nitems, const int* ik,
+                            const int64_t* cols, double* t_out, double* t_minus_out, int* iters_out,
+                            int* status_out) {
+  if (!ctx) return TRANSEC_EINVAL;
+  if (!ctx->have_v || !ctx->have_abc || !ctx->have_k)
+    return ms_fail(ctx, TRANSEC_ESTATE, "potential, absorbing boundary and k-mesh must be set");
+  if (ne < 1 || ne > 1024 || nitems < 0 || !energies || (nitems > 0 && (!ik || !cols || !t_out)))
+    return ms_fail(ctx, TRANSEC_EINVAL, "bad multi-shift arguments (1 <= ne <= 1024)");
+  if (nitems == 0) return TRANSEC_OK;
+  const long long nrhs = (long long)ctx->lplanes.size() * ctx->g.nxy;
+  for (int e = 0; e < ne; ++e)
+    if (!std::isfinite(energies[e])) return ms_fail(ctx, TRANSEC_EINVAL, "non-finite energy");
+  std::vector<MsItem> items(nitems);
+  for (int i = 0; i < nitems; ++i) {
+    if (ik[i] < 0 || ik[i] >= ctx->nk) return ms_fail(ctx, TRANSEC_EINVAL, "k index out of range");
+    if (cols[i] < 0 || cols[i] >= nrhs) return ms_fail(ctx, TRANSEC_EINVAL, "column out of range");
+    items[i] = MsItem{ik[i], RUN_UNIT, 0, 0, (long long)cols[i]};
+  }
+  if (ctx->rplanes.empty()) return ms_fail(ctx, TRANSEC_EINVAL, "right absorbing profile is zero everywhere");
+  DevScope ds(ctx->device);
+  MS_CK(cudaStreamSynchronize(ctx->user));
+  std::vector<double> es(energies, energies + ne), sorted = es;
+  std::sort(sorted.begin(), sorted.end());
+  const double e0 = sorted[ne / 2];
+  // runs in flight: enough point-halves to fill the GPU, bounded by memory
+  const long long n = ctx->g.n;
+  const long long no = (long long)std::max(ctx->lplanes.size(), ctx->rplanes.size()) * ctx->g.nxy;
+  const size_t per_slot = (size_t)4 * 2 * n * 16 + (size_t)2 * ne * 2 * no * 16;
+  long long S = ctx->opts.slots > 0 ? ctx->opts.slots : std::max(1LL, (24LL << 20) / (2 * n));
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) S = std::min<long long>(S, std::max<long long>(1, fr / 2 / per_slot));
+  S = std::max(1LL, std::min<long long>(S, nitems));
+  if (!ctx->sweep) ctx->sweep = new SweepBufs();
+  double* rt = nullptr;
+  int *rit = nullptr, *rst = nullptr;
+  int rc = run_sweep(ctx, items, es, e0, (int)S, 0, 0, 0ULL, &rt, &rit, &rst);
+  int worst = TRANSEC_OK;
+  if (rc == TRANSEC_OK) {
+    std::vector<double> t((size_t)nitems * ne * 2);
+    std::vector<int> it((size_t)nitems * ne), sst((size_t)nitems * ne);
+    cudaError_t e = cudaMemcpy(t.data(), rt, t.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(it.data(), rit, it.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(sst.data(), rst, sst.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = ms_fail(ctx, TRANSEC_ECUDA, std::string("multi-shift results: ") + cudaGetErrorString(e));
+    } else {
+      for (size_t u = 0; u < (size_t)nitems * ne; ++u) {
+        t_out[u] = t[2 * u];
+        if (t_minus_out) t_minus_out[u] = t[2 * u + 1];
+        if (iters_out) iters_out[u] = it[u];
+        if (status_out) status_out[u] = sst[u];
+        if (ms_severity(sst[u]) > ms_severity(worst)) worst = sst[u];
+      }
+    }
+  }
+  cudaFree(rt);
+  cudaFree(rit);
+  cudaFree(rst);
+  if (rc != TRANSEC_OK) return rc;
+  if (worst != TRANSEC_OK) ctx->err = std::string("some columns failed: ") + transec_status_string(worst);
+  return worst;
+}
+
+int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies, int nrep, const int* ik,
+                                int s_left, int s_right, unsigned long long seed, double* T_out,
+                                double* T_minus_out, int* rank_out, int* status_out, int* iters_out) {
+  if (!ctx) return TRANSEC_EINVAL;
+  if (!ctx->have_v || !ctx->have_abc || !ctx->have_k)
+    return ms_fail(ctx, TRANSEC_ESTATE, "potential, absorbing boundary and k-mesh must be set");
+  if (ne < 1 || ne > 1024 || nrep < 0 || !energies || (nrep > 0 && (!ik || !T_out)))
+    return ms_fail(ctx, TRANSEC_EINVAL, "bad sketch arguments (1 <= ne <= 1024)");
+  if (s_left < 1 || s_left > kGnMaxL || s_right < s_left || s_right > kGnMaxR)
+    return ms_fail(ctx, TRANSEC_EINVAL, "sketch sizes must satisfy 1 <= s_left <= 32, s_left <= s_right <= 64");
+  if (nrep == 0) return TRANSEC_OK;
+  for (int e = 0; e < ne; ++e)
+    if (!std::isfinite(energies[e])) return ms_fail(ctx, TRANSEC_EINVAL, "non-finite energy");
+  for (int r = 0; r < nrep; ++r)
+    if (ik[r] < 0 || ik[r] >= ctx->nk) return ms_fail(ctx, TRANSEC_EINVAL, "k index out of range");
+  if (ctx->rplanes.empty()) return ms_fail(ctx, TRANSEC_EINVAL, "right absorbing profile is zero everywhere");
+  DevScope ds(ctx->device);
+  MS_CK(cudaStreamSynchronize(ctx->user));
+  std::vector<double> es(energies, energies + ne), sorted = es;
+  std::sort(sorted.begin(), sorted.end());
+  const double e0 = sorted[ne / 2];
+  const int per = s_left + s_right;
+  std::vector<MsItem> items;
+  std::vector<int> run_slot((size_t)nrep * per);
+  for (int r = 0; r < nrep; ++r) {
+    for (int i = 0; i < s_left; ++i) {
+      run_slot[(size_t)r * per + i] = (int)items.size();
+      items.push_back(MsItem{ik[r], RUN_LEFT, r, i, 0});
+    }
+    for (int i = 0; i < s_right; ++i) {
+      run_slot[(size_t)r * per + s_left + i] = (int)items.size();
+      items.push_back(MsItem{ik[r], RUN_RIGHT, r, i, 0});
+    }
+  }
+  // every run keeps its slot (and its kept planes) until the reduction: S = runs
+  const int S = (int)items.size();
+  if (!ctx->sweep) ctx->sweep = new SweepBufs();
+  double* rt = nullptr;
+  int *rit = nullptr, *rst = nullptr;
+  int rc = run_sweep(ctx, items, es, e0, S, nrep, std::max(s_left, s_right), seed, &rt, &rit, &rst);
+  cudaFree(rt);
+  cudaFree(rit);
+  cudaFree(rst);
+  if (rc != TRANSEC_OK) return rc;
+  SweepBufs& B = *ctx->sweep;
+  int *d_rs = nullptr, *d_rank = nullptr, *d_st = nullptr;
+  double* d_T = nullptr;
+  const size_t nout = (size_t)nrep * ne * 2;
+  cudaError_t e = cudaMalloc(&d_rs, run_slot.size() * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_T, nout * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_rank, nout * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_st, nout * sizeof(int));
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_rs, run_slot.data(), run_slot.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->s);
+  const size_t smem = (size_t)(kGnMaxR * kGnMaxL + kGnMaxR * kGnMaxR) * sizeof(double2);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ms_gn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaEvent_t g0 = nullptr, g1 = nullptr;
+  const bool prof = ctx->opts.profile != 0;
+  if (e == cudaSuccess && prof) {
+    cudaEventCreate(&g0);
+    cudaEventCreate(&g1);
+    cudaEventRecord(g0, ctx->s);
+  }
+  if (e == cudaSuccess) {
+    GnArgs ga{};
+    ga.XS = B.XS; ga.sh = B.sh; ga.run_slot = d_rs; ga.rnd = B.rnd; ga.smax = std::max(s_left, s_right);
+    ga.np = B.no; ga.no = B.no; ga.nxy = ctx->g.nxy; ga.ne = ne; ga.sl = s_left; ga.sr = s_right;
+    ga.lplanes = ctx->d_lplanes; ga.rplanes = ctx->d_rplanes; ga.nlp = (int)ctx->lplanes.size();
+    ga.nrp = (int)ctx->rplanes.size(); ga.gl = ctx->d_gl; ga.gr = ctx->d_gr; ga.T = d_T; ga.rank = d_rank;
+    ga.status = d_st; ga.drop = 1e-13;
+    k_ms_gn<<<dim3((unsigned)ne, (unsigned)nrep, 2), 256, smem, ctx->s>>>(ga);
+    ctx->launches += 1;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && prof) cudaEventRecord(g1, ctx->s);
+  std::vector<double> T(nout);
+  std::vector<int> rk(nout), stt(nout);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(T.data(), d_T, nout * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rk.data(), d_rank, nout * sizeof(int), cudaMemcpyDeviceToHost, ctx->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stt.data(), d_st, nout * sizeof(int), cudaMemcpyDeviceToHost, ctx->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
+  if (e == cudaSuccess && prof) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g0, g1) == cudaSuccess) ctx->sweep_reduce_ms += ms;
+  }
+  if (g0) cudaEventDestroy(g0);
+  if (g1) cudaEventDestroy(g1);
+  // seed iterations per group: the longest run of the group
+  std::vector<MsShift> hsh;
+  if (e == cudaSuccess && iters_out) {
+    hsh.resize((size_t)S * ne);
+    e = cudaMemcpy(hsh.data(), B.sh, hsh.size() * sizeof(MsShift), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(d_rs);
+  cudaFree(d_T);
+  cudaFree(d_rank);
+  cudaFree(d_st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return ms_fail(ctx, TRANSEC_ECUDA, std::string("sketch reduction: ") + cudaGetErrorString(e));
+  }
+  int worst = TRANSEC_OK;
+  for (int r = 0; r < nrep; ++r)
+    for (int s = 0; s < ne; ++s) {
+      const size_t o = ((size_t)r * ne + s) * 2;
+      const size_t u = (size_t)r * ne + s;
+      T_out[u] = T[o];
+      if (T_minus_out) T_minus_out[u] = T[o + 1];
+      if (rank_out) rank_out[u] = std::min(rk[o], rk[o + 1]);
+      const int w = ms_severity(stt[o]) >= ms_severity(stt[o + 1]) ? stt[o] : stt[o + 1];
+      if (status_out) status_out[u] = w;
+      if (ms_severity(w) > ms_severity(worst)) worst = w;
+      if (iters_out) {
+        int mx = 0;
+        for (int c = 0; c < per; ++c) mx = std::max(mx, hsh[(size_t)run_slot[(size_t)r * per + c] * ne + s].conv_it);
+        iters_out[u] = mx;
+      }
+    }
+  if (worst != TRANSEC_OK) ctx->err = std::string("some (E, k) failed: ") + transec_status_string(worst);
+  return worst;
+}
+
+}  // extern "C"

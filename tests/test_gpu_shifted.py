@@ -3,8 +3,7 @@ the oracle's dense LU, through the C ABI.
 
 Every energy's column contribution t_j (and the shadow system's t_j at -k) must match
 dense LU to the solver's 1e-6 bar; the run takes as many seed iterations as its slowest
-energy, far fewer than the separate solves together.  (Named to run after the other
-GPU tests.)"""
+energy, far fewer than the separate solves together."""
 
 import numpy as np
 import pytest

@@ -1,0 +1,127 @@
+"""The multi-shift slot engine and the two-sided sketch, through the C ABI.
+
+* transec_shifted_columns: every column at every energy of a window from one Krylov
+  run per column (A(E, k) = A(E0, k) + (E - E0) 1, Sec. II.A), against the oracle's
+  dense LU at k and at -k (the shadow system, A(E, k)^T = A(E, -k), Sec. II.B), and
+  against the plain engine's separate solves; runs that retire and refill give the
+  same numbers as runs that all fit at once.
+* transec_transmission_sketch: the full trace T(E, k) = 4 Tr[Gamma_L G^dagger Gamma_R G]
+  from random left and right right-hand sides, against the dense-LU full trace over
+  every left-CAP column, at k and -k, within |dT| <= 1e-6 (the metric's bar).
+"""
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import context, library, need_gpu
+from workloads import small_instance
+from oracle.transmission import left_support, transmission_dense
+
+pytestmark = pytest.mark.gpu
+
+TOL_T = 1e-6
+
+
+def _inst(kf, seed=5, nx=6, ny=5, nz=40, order=8, ncap=8):
+    return small_instance(nx, ny, nz, 0.45, order, ncap, v_amp=0.7, kfrac=(kf, (-kf[0], -kf[1])),
+                          energies=(0.3,), seed=seed)
+
+
+def _dense_cols(inst, e, kf, cols):
+    g = inst.grid
+    return transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf, cols)[1]
+
+
+def test_shifted_columns_match_dense_lu_at_both_k():
+    need_gpu()
+    kf = (0.21, -0.34)
+    inst = _inst(kf)
+    g = inst.grid
+    energies = np.linspace(0.12, 0.78, 9)
+    sup = left_support(g, inst.gamma_l)
+    cols = np.array([0, 17, 101, 239], np.int64)
+    with context(inst) as tr:
+        r = tr.shifted_columns(energies, np.zeros(cols.size, np.int32), cols)
+    assert np.all(r["status"] == 0), r["status"]
+    for s, e in enumerate(energies):
+        ref_p = _dense_cols(inst, e, kf, sup[cols])
+        ref_m = _dense_cols(inst, e, (-kf[0], -kf[1]), sup[cols])
+        assert np.abs(r["t"][:, s] - ref_p).max() <= TOL_T * 1e-3, (e, r["t"][:, s], ref_p)
+        assert np.abs(r["t_minus"][:, s] - ref_m).max() <= TOL_T * 1e-3, (e, r["t_minus"][:, s], ref_m)
+    # the run length is set by the slowest energy; every energy reports its own stop
+    assert np.all(r["iters"] > 0) and np.all(r["iters"].max(axis=1) >= r["iters"].min(axis=1))
+
+
+def test_shifted_columns_agree_with_separate_solves_and_refill():
+    need_gpu()
+    kf = (0.4375, 0.1875)
+    inst = _inst(kf, seed=9, nx=5, ny=6, nz=36, order=12, ncap=7)
+    energies = np.array([0.2, 0.35, 0.5, 0.65])
+    cols = np.array([3, 44, 90, 131, 170], np.int64)
+    ik = np.zeros(cols.size, np.int32)
+    with context(inst, tol=1e-11) as tr:
+        all_in = tr.shifted_columns(energies, ik, cols)
+        tr.set_solver(slots=2)  # five runs through two slots: retire and refill on the GPU
+        refill = tr.shifted_columns(energies, ik, cols)
+        tr.set_solver(slots=0)
+        sep = [tr.column_contributions(np.full(cols.size, e), ik, cols) for e in energies]
+    assert np.all(all_in["status"] == 0) and np.all(refill["status"] == 0)
+    np.testing.assert_array_equal(all_in["t"], refill["t"])
+    np.testing.assert_array_equal(all_in["t_minus"], refill["t_minus"])
+    for s in range(energies.size):
+        assert np.abs(all_in["t"][:, s] - sep[s]["t"]).max() <= 1e-9
+        assert np.abs(all_in["t_minus"][:, s] - sep[s]["t_minus"]).max() <= 1e-9
+
+
+@pytest.mark.parametrize("kf,order", [((0.23, -0.37), 8), ((0.0, 0.0), 4), ((0.4375, 0.3125), 12)])
+def test_sketch_full_trace_matches_dense_lu(kf, order):
+    need_gpu()
+    inst = _inst(kf, seed=13, nx=6, ny=6, nz=44, order=order, ncap=9)
+    g = inst.grid
+    energies = np.linspace(0.1, 0.9, 7)
+    with context(inst) as tr:
+        r = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=3)
+    assert np.all(r["status"] == 0), r["status"]
+    for s, e in enumerate(energies):
+        tp, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf)
+        tm, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, (-kf[0], -kf[1]))
+        assert abs(r["T"][0, s] - tp) <= TOL_T, (e, r["T"][0, s], tp)
+        assert abs(r["T_minus"][0, s] - tm) <= TOL_T, (e, r["T_minus"][0, s], tm)
+        assert 1 <= r["rank"][0, s] <= 8
+
+
+def test_sketch_two_k_groups_and_seeds():
+    """Two k-points in one call (independent run groups), and a second random draw:
+    both estimates agree with dense LU."""
+    need_gpu()
+    kf1, kf2 = (0.3125, -0.1875), (-0.0625, 0.4375)
+    inst = small_instance(5, 5, 40, 0.45, 8, 8, v_amp=0.7, kfrac=(kf1, kf2), energies=(0.3,), seed=21)
+    g = inst.grid
+    energies = np.array([0.25, 0.55])
+    with context(inst) as tr:
+        a = tr.transmission_sketch(energies, [0, 1], s_left=6, s_right=12, seed=1)
+        b = tr.transmission_sketch(energies, [1, 0], s_left=6, s_right=12, seed=2)
+    for r, order in ((a, (kf1, kf2)), (b, (kf2, kf1))):
+        assert np.all(r["status"] == 0)
+        for q, kf in enumerate(order):
+            for s, e in enumerate(energies):
+                tp, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf)
+                assert abs(r["T"][q, s] - tp) <= TOL_T
+
+
+def test_sweep_argument_checks():
+    need_gpu()
+    pkg = library()
+    inst = _inst((0.1, 0.2))
+    with context(inst) as tr:
+        for bad in (dict(s_left=0, s_right=4), dict(s_left=8, s_right=4), dict(s_left=33, s_right=40),
+                    dict(s_left=4, s_right=65)):
+            with pytest.raises(pkg.TransecError) as ei:
+                tr.transmission_sketch([0.3], [0], **bad)
+            assert ei.value.status == pkg.EINVAL
+        with pytest.raises(pkg.TransecError):
+            tr.transmission_sketch([0.3], [5])
+        with pytest.raises(pkg.TransecError):
+            tr.shifted_columns([0.3], [0], [10 ** 6])
+        with pytest.raises(pkg.TransecError):
+            tr.shifted_columns([float("nan")], [0], [1])
