@@ -66,8 +66,13 @@ enum transec_method {
 /* Arithmetic of the iteration. */
 enum transec_precision {
   TRANSEC_PREC_FP64 = 0,  /* complex128 vectors and stencil throughout */
-  TRANSEC_PREC_MIXED = 1  /* complex64 vectors and stencil with FP64 scalars, FP64
+  TRANSEC_PREC_MIXED = 1, /* complex64 vectors and stencil with FP64 scalars, FP64
                              solution accumulation and FP64 residual replacement */
+  TRANSEC_PREC_DF64 = 2   /* multi-shift engine only (transec_shifted_columns,
+                             transec_transmission_sketch): vectors stored and the stencil,
+                             vector and per-shift updates computed in double-float (pairs
+                             of floats, ~2^-47 relative rounding) on the FP32 pipes, Krylov
+                             scalars in FP64; the other solvers run it as FP64 */
 };
 
 typedef struct transec_solver_opts {

@@ -11,7 +11,7 @@ import numpy as np
 
 from .binding import (  # noqa: F401
     EBREAKDOWN, ECUDA, EINVAL, ENOCONV, ENOMEM, ESTATE, ETIMEOUT, METHOD_AUTO, METHOD_BICG,
-    METHOD_COCG, OK, PREC_FP64, PREC_MIXED, SolverOpts, TransecError, load,
+    METHOD_COCG, OK, PREC_DF64, PREC_FP64, PREC_MIXED, SolverOpts, TransecError, load,
     transec_apply, transec_apply_noalloc, transec_autotune, transec_batch_column_contributions,
     transec_column_contributions, transec_create, transec_destroy,
     transec_get_solver, transec_last_error, transec_n_rhs, transec_set_abc,

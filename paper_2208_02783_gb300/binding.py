@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_native", "libtransec.so")
 # status codes (enum transec_status)
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 METHOD_AUTO, METHOD_COCG, METHOD_BICG = 0, 1, 2
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_DF64 = 0, 1, 2
 
 
 class TransecError(RuntimeError):

@@ -992,7 +992,7 @@ int transec_set_kmesh(transec_ctx* ctx, int nk, const double* kfrac, const doubl
 int transec_set_solver(transec_ctx* ctx, const transec_solver_opts* opts) {
   if (!ctx || !opts) return TRANSEC_EINVAL;
   transec_solver_opts o = *opts;
-  if (o.method < 0 || o.method > 2 || o.precision < 0 || o.precision > 1 || o.tol < 0 ||
+  if (o.method < 0 || o.method > 2 || o.precision < 0 || o.precision > 2 || o.tol < 0 ||
       o.maxit < 0 || o.slots < 0 || o.chunk < 0 || o.tile_y < 0 || o.slab < 0 || o.mixed_maxit < 0 ||
       !std::isfinite(o.tol) || !std::isfinite(o.reliable))
     return fail(ctx, TRANSEC_EINVAL, "invalid solver options");

@@ -1,0 +1,261 @@
+// The hot kernels of the multi-shift engine in double-float arithmetic (df64.cuh):
+//
+//   k_stencil_df   p <- r + beta p, q <- A(E0, +-k) p, sigma += <p~, q> (pairing form)
+//   k_update_df    r -= alpha q, rho' = <r~, r>, ||r_h||^2
+//   k_ms_shift_df  per-shift p_sigma, x_sigma on the kept planes
+//
+// The same operator and launch structure as the FP64 kernels of kernels.cuh (paper
+// Sec. II.A, Eqs. Bloch and H_k: the order-2R stencil in pair form, Bloch-phased
+// lateral wraps, Dirichlet ends in z; half 1 applies A(E, -k) = A(E, k)^T, Sec. II.B),
+// with complex vectors stored as float4 double-float values and all arithmetic on the
+// FP32 pipes.  The bilinear forms are accumulated in double-float on vectors scaled
+// by 2^k (k per run, from the last residual norm) so that small residuals stay well
+// inside the float exponent range; the per-block partial sums are returned in FP64.
+#pragma once
+
+#include "df64.cuh"
+#include "kernels.cuh"
+
+namespace transec {
+
+struct StencilDfArgs {
+  const float4* r;        // [slot][half][n]
+  const float4* p_in;
+  float4* p_out;          // r + beta p_in
+  float4* q;              // A p_out
+  double* part;           // [slot][nblk][2] partial sums of <p~, A p>
+  const Slot* slots;
+  const int* escale;      // [slot] k: the pairing dot is taken on 2^k p and 2^k A p
+  const float4* phase;    // [nk][2][2][kPhaseN] Bloch phases, complex df64
+  const float2* v;        // V per point, df64 (hi, lo)
+  const float2* gam;      // Gamma_L + Gamma_R per plane, df64
+  float2 kx[kMaxR + 1], ky[kMaxR + 1], kz[kMaxR + 1];  // c_m / (2 h^2), df64
+  double diag_c;          // c_0/2 sum_a h_a^-2
+  int nx, ny, nz;
+  long long nxy, n;
+  int H, TX, TY, D, ntx, conj;
+  long long slot_stride;
+};
+
+constexpr int kDfThreads = 448;
+
+// 2^k as a float (|k| <= 126), exact
+__device__ inline float pow2f(int k) {
+  k = max(-126, min(126, k));
+  return __int_as_float((k + 127) << 23);
+}
+
+// unnormalised a + b: the TwoSum of the high parts, low parts gathered
+__device__ inline df df_pair(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return df{s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo))};
+}
+
+__device__ inline df acc_df(const dfacc& a) { return df{a.hi, a.lo}; }
+
+template <int R>
+__global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[2][32];
+  float4* sm = reinterpret_cast<float4*>(smem_raw);
+
+  const int slot = blockIdx.z;
+  const Slot* stp = a.slots + slot;
+  if (stp->status != SLOT_ACTIVE) return;  // uniform over the block
+  const dfc beta = dfc{df_split(stp->beta.x), df_split(stp->beta.y)};
+  const df ediag = df_split(stp->e + a.diag_c);
+  const int ik = stp->ik;
+  const int ks = a.escale[slot];
+  const float sc = pow2f(ks);
+
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const long long nxy = a.nxy;
+  const int TX = a.TX, TY = a.TY, D = a.D, ntx = a.ntx;
+  const int npt = TX * TY;
+  const int t = threadIdx.x;
+  const bool worker = t < npt * a.H;
+  const int half = worker ? t / npt : 0;
+  const int lt = worker ? t - half * npt : 0;
+  const int tx = lt % TX, ty = lt / TX;
+  const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * TY;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool inside = worker && (gx < nx) && (gy < ny);
+  const int z0 = blockIdx.y * D;
+  const int z1 = min(z0 + D, nz);
+  const int SW = TX + 2 * R;
+  const int SHt = TY + 2 * R;
+  float4* my = sm + half * SW * SHt;
+  const long long base = (long long)slot * a.slot_stride + (long long)half * a.n;
+  const float4* __restrict__ r = a.r + base;
+  const float4* __restrict__ pin = a.p_in + base;
+  float4* __restrict__ pout = a.p_out + base;
+  float4* __restrict__ q = a.q + base;
+  const float4* ph = a.phase + (size_t)(ik * 2 + (half ^ a.conj)) * 2 * kPhaseN;
+  const long long pidx = (long long)gx + (long long)nx * gy;
+
+  auto pnew = [&](long long off) -> dfc { return dfc_fma(beta, dfc_load(pin[off]), dfc_load(r[off])); };
+  // p_new at a lateral position of plane zc, wrapped into the cell with its Bloch
+  // factor (Eq. Bloch)
+  auto wrapped = [&](int xx, int yy, int zc) -> dfc {
+    int wx = 0, wy = 0;
+    if (xx < 0 || xx >= nx) { wx = floordiv(xx, nx); xx -= wx * nx; }
+    if (yy < 0 || yy >= ny) { wy = floordiv(yy, ny); yy -= wy * ny; }
+    dfc v = pnew((long long)zc * nxy + xx + (long long)nx * yy);
+    if (wx) v = dfc_mul(v, dfc_load(ph[kPhaseW + wx]));
+    if (wy) v = dfc_mul(v, dfc_load(ph[kPhaseN + kPhaseW + wy]));
+    return v;
+  };
+
+  dfc qv[2 * R + 1];
+  qv[0] = dfc_zero();
+#pragma unroll
+  for (int m = 1; m <= 2 * R; ++m) {
+    const int z = z0 - R + m - 1;
+    qv[m] = (inside && z >= 0 && z < nz) ? pnew((long long)z * nxy + pidx) : dfc_zero();
+  }
+
+  dfacc sg_re, sg_im;
+  const int nh = 2 * R * (TX + TY);
+  for (int zc = z0; zc < z1; ++zc) {
+#pragma unroll
+    for (int m = 0; m < 2 * R; ++m) qv[m] = qv[m + 1];
+    {
+      const int z = zc + R;
+      qv[2 * R] = (inside && z < nz) ? pnew((long long)z * nxy + pidx) : dfc_zero();
+    }
+    const dfc c = qv[R];
+    if (worker) my[(ty + R) * SW + tx + R] = dfc_store(inside ? c : wrapped(gx, gy, zc));
+    for (int h = worker ? lt : nh; h < nh; h += npt) {
+      int hx, hy;
+      if (h < 2 * R * TY) {
+        const int row = h / (2 * R), k = h - row * 2 * R;
+        hy = row + R;
+        hx = (k < R) ? k : TX + k;
+      } else {
+        const int h2 = h - 2 * R * TY;
+        const int col = h2 / (2 * R), k = h2 - col * 2 * R;
+        hx = col + R;
+        hy = (k < R) ? k : TY + k;
+      }
+      my[hy * SW + hx] = dfc_store(wrapped(x0 + hx - R, y0 + hy - R, zc));
+    }
+    __syncthreads();
+    if (inside) {
+      const long long off = (long long)zc * nxy + pidx;
+      const float2 vv = a.v[off];
+      const df dr = df_sub(ediag, df{vv.x, vv.y});
+      const float2 gg = a.gam[zc];
+      const df di = df{gg.x, gg.y};
+      // per-axis accumulators keep independent dependency chains
+      dfacc dre, dim_, xre, xim, yre, yim, zre, zim;
+      dre.add(df_mul_raw(dr, c.re));
+      dre.add(df_neg(df_mul_raw(di, c.im)));
+      dim_.add(df_mul_raw(dr, c.im));
+      dim_.add(df_mul_raw(di, c.re));
+      const float4* ctr = my + (ty + R) * SW + (tx + R);
+#pragma unroll
+      for (int m = 1; m <= R; ++m) {
+        const float4 xa = ctr[m], xb = ctr[-m], ya = ctr[m * SW], yb = ctr[-m * SW];
+        const dfc za = qv[R + m], zb = qv[R - m];
+        const df ckx = df{a.kx[m].x, a.kx[m].y}, cky = df{a.ky[m].x, a.ky[m].y},
+                 ckz = df{a.kz[m].x, a.kz[m].y};
+        xre.add(df_mul_raw(df_pair(df{xa.x, xa.y}, df{xb.x, xb.y}), ckx));
+        xim.add(df_mul_raw(df_pair(df{xa.z, xa.w}, df{xb.z, xb.w}), ckx));
+        yre.add(df_mul_raw(df_pair(df{ya.x, ya.y}, df{yb.x, yb.y}), cky));
+        yim.add(df_mul_raw(df_pair(df{ya.z, ya.w}, df{yb.z, yb.w}), cky));
+        zre.add(df_mul_raw(df_pair(za.re, zb.re), ckz));
+        zim.add(df_mul_raw(df_pair(za.im, zb.im), ckz));
+      }
+      dre.add(acc_df(xre));
+      dre.add(acc_df(yre));
+      dre.add(acc_df(zre));
+      dim_.add(acc_df(xim));
+      dim_.add(acc_df(yim));
+      dim_.add(acc_df(zim));
+      const dfc acc = dfc{dre.value(), dim_.value()};
+      q[off] = dfc_store(acc);
+      pout[off] = dfc_store(c);
+      // pairing form: half h pairs with half 1-h at the same point (or itself)
+      const dfc o = (a.H == 2) ? dfc_load(sm[(1 - half) * SW * SHt + (ty + R) * SW + tx + R]) : c;
+      dfc_dot_add(sg_re, sg_im, dfc{df_scale(o.re, sc), df_scale(o.im, sc)},
+                  dfc{df_scale(acc.re, sc), df_scale(acc.im, sc)});
+    }
+    __syncthreads();
+  }
+  const double unscale = ldexp(1.0, -2 * max(-126, min(126, ks)));
+  double v2[2] = {df_value(sg_re.value()) * unscale, df_value(sg_im.value()) * unscale};
+  block_sum<2>(v2, red);
+  if (threadIdx.x == 0) {
+    const int nblk = gridDim.x * gridDim.y;
+    const int b = blockIdx.x + gridDim.x * blockIdx.y;
+    double* o = a.part + ((size_t)slot * nblk + b) * 2;
+    o[0] = v2[0];
+    o[1] = v2[1];
+  }
+}
+
+struct UpdateDfArgs {
+  float4* r;
+  const float4* q;
+  const double* sig_part;  // [slot][sig_nblk][2]
+  int sig_nblk;
+  double* rho_part;        // [slot][gridDim.x][4]: rho re, rho im, |r_0|^2, |r_1|^2
+  const Slot* slots;
+  const int* escale;
+  long long n, slot_stride;
+  int H;
+};
+
+// r -= alpha q on both halves, partial <r~, r> (pairing form) and ||r_h||^2.
+// grid (blocks, slots), 256 threads
+__global__ void __launch_bounds__(256) k_update_df(const UpdateDfArgs a) {
+  __shared__ double red[4][32];
+  __shared__ double2 s_alpha;
+  const int slot = blockIdx.y;
+  const Slot* stp = a.slots + slot;
+  if (stp->status != SLOT_ACTIVE) return;
+  if (threadIdx.x < 32) {
+    const double2 al = slot_alpha(a.sig_part + (size_t)slot * a.sig_nblk * 2, a.sig_nblk, stp->rho);
+    if (threadIdx.x == 0) s_alpha = al;
+  }
+  __syncthreads();
+  const dfc mal = dfc{df_split(-s_alpha.x), df_split(-s_alpha.y)};
+  const int ks = a.escale[slot];
+  const float sc = pow2f(ks);
+  const long long n = a.n;
+  const long long base = (long long)slot * a.slot_stride;
+  dfacc rr_re, rr_im;
+  float n0 = 0.f, n1 = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    dfc rv[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (h >= a.H) break;
+      const long long off = base + (long long)h * n + i;
+      rv[h] = dfc_fma(mal, dfc_load(a.q[off]), dfc_load(a.r[off]));
+      a.r[off] = dfc_store(rv[h]);
+    }
+    const dfc s0 = dfc{df_scale(rv[0].re, sc), df_scale(rv[0].im, sc)};
+    n0 = __fmaf_rn(s0.re.hi, s0.re.hi, __fmaf_rn(s0.im.hi, s0.im.hi, n0));
+    if (a.H == 2) {
+      const dfc s1 = dfc{df_scale(rv[1].re, sc), df_scale(rv[1].im, sc)};
+      n1 = __fmaf_rn(s1.re.hi, s1.re.hi, __fmaf_rn(s1.im.hi, s1.im.hi, n1));
+      dfc_dot_add(rr_re, rr_im, s0, s1);  // <r, r> = 2 r_+ . r_-
+    } else {
+      dfc_dot_add(rr_re, rr_im, s0, s0);
+    }
+  }
+  const double unscale = ldexp(1.0, -2 * max(-126, min(126, ks)));
+  const double rscale = (a.H == 2 ? 2.0 : 1.0) * unscale;
+  double v4[4] = {rscale * df_value(rr_re.value()), rscale * df_value(rr_im.value()), unscale * (double)n0,
+                  unscale * (double)n1};
+  block_sum<4>(v4, red);
+  if (threadIdx.x == 0) {
+    double* o = a.rho_part + ((size_t)slot * gridDim.x + blockIdx.x) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[k] = v4[k];
+  }
+}
+
+}  // namespace transec

@@ -40,6 +40,7 @@
 #include <vector>
 
 #include "engine.cuh"
+#include "stencil_df.cuh"
 
 namespace transec {
 template <typename T>
@@ -75,6 +76,7 @@ struct MsShift {
 // Coefficients of one iteration's shifted update (k_ms_coef -> k_ms_shift).
 struct MsCoef {
   double2 inv_pi, beta_s, alpha_s;
+  float4 inv_pi_df, beta_s_df, alpha_s_df;  // the same in double-float
 };
 
 // One queued run.
@@ -99,6 +101,11 @@ struct SweepBufs {
   double* energies = nullptr;
   double2* rnd = nullptr;
   int *lrank = nullptr, *rrank = nullptr;
+  int* escale = nullptr;       // [S] double-float form: 2^k scaling of the bilinear forms
+  float2* v_df = nullptr;      // V, Gamma and Bloch phases in double-float
+  float2* gam_df = nullptr;
+  float4* phase_df = nullptr;
+  size_t cap_n = 0, cap_ph = 0;
   // capacities (elements) of the buffers above, kept between calls
   size_t cap_vec = 0, cap_shv = 0, cap_sig = 0, cap_rho = 0, cap_slots = 0, cap_shs = 0;
   size_t cap_items = 0, cap_ene = 0, cap_rnd = 0, cap_nz = 0;
@@ -106,7 +113,8 @@ struct SweepBufs {
     cudaFree(R); cudaFree(P0); cudaFree(P1); cudaFree(Q); cudaFree(XS); cudaFree(PS);
     cudaFree(sig_part); cudaFree(rho_part); cudaFree(slots); cudaFree(ms); cudaFree(sh);
     cudaFree(coef); cudaFree(queue); cudaFree(items); cudaFree(energies); cudaFree(rnd);
-    cudaFree(lrank); cudaFree(rrank);
+    cudaFree(lrank); cudaFree(rrank); cudaFree(escale); cudaFree(v_df); cudaFree(gam_df);
+    cudaFree(phase_df);
     *this = SweepBufs{};
   }
 };
@@ -156,6 +164,22 @@ __global__ void __launch_bounds__(256) k_ms_random(const RandomArgs a) {
 }
 
 // ---------------------------------------------------------------------------------
+// storage of the vectors: complex FP64 (double2) or double-float (float4); the
+// kernels off the hot path read and write them through FP64 values
+// ---------------------------------------------------------------------------------
+
+__device__ inline double2 vload(const double2* p, long long i) { return p[i]; }
+__device__ inline double2 vload(const float4* p, long long i) { return dfc_to_double2(p[i]); }
+__device__ inline void vstore(double2* p, long long i, double2 v) { p[i] = v; }
+__device__ inline void vstore(float4* p, long long i, double2 v) { p[i] = dfc_from_double2(v); }
+
+// exponent k with 2^k x of order one (clamped to the float range)
+__device__ inline int unit_exponent(double x) {
+  if (!(x > 0.0) || !isfinite(x)) return 0;
+  return max(-120, min(120, -ilogb(x)));
+}
+
+// ---------------------------------------------------------------------------------
 // queue: assignment, vector initialisation, rho_0
 // ---------------------------------------------------------------------------------
 
@@ -190,6 +214,7 @@ struct MsArgs {
   int nblk_st;
   double tol;
   int maxit;
+  int* escale;             // [S]
   // UNIT results: [item][shift][2] t, [item][shift] iterations and status
   double* res_t;
   int* res_it;
@@ -227,13 +252,17 @@ __global__ void k_ms_assign(const MsArgs a) {
     m.rep = it.rep;
     m.idx = it.idx;
     a.ms[s] = m;
+    a.escale[s] = 0;
     ++next;
   }
   q->next = next;
 }
 
 // r = b on both halves, p = 0, for newly assigned slots.  grid (blocks, S)
+template <typename V>
 __global__ void __launch_bounds__(256) k_ms_init(const MsArgs a) {
+  V* R = reinterpret_cast<V*>(a.R);
+  V* P0 = reinterpret_cast<V*>(a.P0);
   const int slot = blockIdx.y;
   const Slot& st = a.slots[slot];
   if (!st.init) return;
@@ -264,8 +293,8 @@ __global__ void __launch_bounds__(256) k_ms_init(const MsArgs a) {
     }
     for (int h = 0; h < 2; ++h) {
       const long long off = (long long)slot * 2 * a.n + (long long)h * a.n + i;
-      a.R[off] = b;
-      a.P0[off] = make_double2(0.0, 0.0);
+      vstore(R, off, b);
+      vstore(P0, off, make_double2(0.0, 0.0));
     }
   }
 }
@@ -293,6 +322,7 @@ __global__ void __launch_bounds__(256) k_ms_init_shift(const MsArgs a) {
 
 // rho_0 = 2 b.b (pairing form of the two equal halves) and ||b|| of new random runs.
 // grid S, 256 threads
+template <typename V>
 __global__ void __launch_bounds__(256) k_ms_rho0(const MsArgs a) {
   __shared__ double red[3][32];
   const int slot = blockIdx.x;
@@ -302,10 +332,10 @@ __global__ void __launch_bounds__(256) k_ms_rho0(const MsArgs a) {
   if (m.kind == RUN_UNIT) return;
   const int* planes = m.kind == RUN_LEFT ? a.lplanes : a.rplanes;
   const long long np = (long long)(m.kind == RUN_LEFT ? a.nlp : a.nrp) * a.nxy;
-  const double2* r = a.R + (long long)slot * 2 * a.n;
+  const V* r = reinterpret_cast<const V*>(a.R) + (long long)slot * 2 * a.n;
   double v[3] = {0.0, 0.0, 0.0};
   for (long long u = threadIdx.x; u < np; u += blockDim.x) {
-    const double2 b = r[(long long)planes[u / a.nxy] * a.nxy + u % a.nxy];
+    const double2 b = vload(r, (long long)planes[u / a.nxy] * a.nxy + u % a.nxy);
     v[0] += b.x * b.x - b.y * b.y;
     v[1] += 2.0 * b.x * b.y;
     v[2] += b.x * b.x + b.y * b.y;
@@ -314,6 +344,7 @@ __global__ void __launch_bounds__(256) k_ms_rho0(const MsArgs a) {
   if (threadIdx.x == 0) {
     st.rho = make_double2(2.0 * v[0], 2.0 * v[1]);
     m.bnorm = sqrt(v[2]);
+    a.escale[slot] = unit_exponent(m.bnorm);
   }
 }
 
@@ -359,6 +390,9 @@ __global__ void __launch_bounds__(256) k_ms_coef(const MsArgs a) {
     co.inv_pi = cdiv(make_double2(1.0, 0.0), z.pi);
     const double2 ratio = cdiv(z.pi_prev, z.pi);
     co.beta_s = cmul(cmul(ratio, ratio), bp);
+    co.inv_pi_df = dfc_from_double2(co.inv_pi);
+    co.beta_s_df = dfc_from_double2(co.beta_s);
+    co.alpha_s_df = dfc_from_double2(co.alpha_s);
     a.coef[(long long)slot * a.ne + s] = co;
   }
 }
@@ -385,6 +419,33 @@ __global__ void __launch_bounds__(256) k_ms_shift(const MsArgs a) {
     pv = cadd(cmul(rv, co.inv_pi), cmul(co.beta_s, pv));
     a.PS[off] = pv;
     a.XS[off] = cadd(a.XS[off], cmul(co.alpha_s, pv));
+  }
+}
+
+// The same in double-float storage and arithmetic.
+__global__ void __launch_bounds__(256) k_ms_shift_df(const MsArgs a) {
+  const int slot = blockIdx.z, s = blockIdx.y;
+  if (a.slots[slot].status != SLOT_ACTIVE) return;
+  const long long zs = (long long)slot * a.ne + s;
+  if (!a.sh[zs].active) return;
+  const MsCoef& cf = a.coef[zs];
+  const dfc inv_pi = dfc_load(cf.inv_pi_df), beta_s = dfc_load(cf.beta_s_df), alpha_s = dfc_load(cf.alpha_s_df);
+  const int kind = a.ms[slot].kind;
+  const int* planes = kind == RUN_RIGHT ? a.lplanes : a.rplanes;
+  const long long nro = (long long)(kind == RUN_RIGHT ? a.nlp : a.nrp) * a.nxy;
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= nro) return;
+  const long long pt = (long long)planes[u / a.nxy] * a.nxy + u % a.nxy;
+  const float4* R = reinterpret_cast<const float4*>(a.R);
+  float4* PS = reinterpret_cast<float4*>(a.PS);
+  float4* XS = reinterpret_cast<float4*>(a.XS);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const dfc rv = dfc_load(R[(long long)slot * 2 * a.n + (long long)h * a.n + pt]);
+    const long long off = (zs * 2 + h) * a.no + u;
+    const dfc pv = dfc_add(dfc_mul(rv, inv_pi), dfc_mul(beta_s, dfc_load(PS[off])));
+    PS[off] = dfc_store(pv);
+    XS[off] = dfc_store(dfc_fma(alpha_s, pv, dfc_load(XS[off])));
   }
 }
 
@@ -452,12 +513,14 @@ __global__ void __launch_bounds__(256) k_ms_scalars(const MsArgs a) {
       st.beta = cdiv(rho_new, st.rho);
       st.rho = rho_new;
       a.ms[slot].alpha_prev = a.ms[slot].alpha;
+      a.escale[slot] = unit_exponent(rn);
     }
   }
 }
 
 // UNIT runs that finished: t_j = 4 Gamma_L(j) sum_R Gamma_R |x_sigma|^2 per shift and
 // half.  grid (ne, S), 256 threads
+template <typename V>
 __global__ void __launch_bounds__(256) k_ms_trace(const MsArgs a) {
   __shared__ double red[2][32];
   const int s = blockIdx.x, slot = blockIdx.y;
@@ -467,10 +530,10 @@ __global__ void __launch_bounds__(256) k_ms_trace(const MsArgs a) {
   const long long nro = (long long)a.nrp * a.nxy;
   double v[2] = {0.0, 0.0};
   for (int h = 0; h < 2; ++h) {
-    const double2* x = a.XS + (zs * 2 + h) * a.no;
+    const V* x = reinterpret_cast<const V*>(a.XS) + (zs * 2 + h) * a.no;
     double acc = 0.0;
     for (long long u = threadIdx.x; u < nro; u += blockDim.x) {
-      const double2 xv = x[u];
+      const double2 xv = vload(x, u);
       acc += a.gr[a.rplanes[u / a.nxy]] * (xv.x * xv.x + xv.y * xv.y);
     }
     v[h] = acc;
@@ -540,7 +603,10 @@ __device__ inline void gn_block_sum(double (&v)[NV], double* s_out, double (*red
 
 constexpr int kGnChunk = 8;
 
-// grid (ne, nrep, 2 signs), 256 threads, dynamic shared memory for K and G_b
+// grid (ne, nrep, 2 signs), 256 threads, dynamic shared memory for K and G_b.  V is
+// the storage of the kept planes; the LEFT runs' planes are rewritten in place as
+// complex FP64 (Y, then Q).
+template <typename V>
 __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
   extern __shared__ __align__(16) unsigned char gn_smem[];
   __shared__ double red[2 * kGnChunk][32];
@@ -576,14 +642,19 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
     return;
   }
   const long long nR = (long long)a.nrp * a.nxy, nL = (long long)a.nlp * a.nxy;
-  auto ycol = [&](int c) { return a.XS + (((long long)rs[c] * a.ne + s) * 2 + hY) * a.no; };
-  auto wcol = [&](int i) { return a.XS + (((long long)rs[sl + i] * a.ne + s) * 2 + hW) * a.no; };
-  // Y = Gamma_R^1/2 x on the right-CAP planes, in place
+  V* xs = reinterpret_cast<V*>(a.XS);
+  auto ycol = [&](int c) {
+    return reinterpret_cast<double2*>(xs + (((long long)rs[c] * a.ne + s) * 2 + hY) * a.no);
+  };
+  auto wcol = [&](int i) -> const V* { return xs + (((long long)rs[sl + i] * a.ne + s) * 2 + hW) * a.no; };
+  // Y = Gamma_R^1/2 x on the right-CAP planes, in place as complex FP64
   for (int c = 0; c < sl; ++c) {
+    const V* yv = xs + (((long long)rs[c] * a.ne + s) * 2 + hY) * a.no;
     double2* y = ycol(c);
     for (long long u = threadIdx.x; u < nR; u += blockDim.x) {
       const double g = sqrt(a.gr[a.rplanes[u / a.nxy]]);
-      y[u] = make_double2(g * y[u].x, g * y[u].y);
+      const double2 xv = vload(yv, u);
+      y[u] = make_double2(g * xv.x, g * xv.y);
     }
   }
   __syncthreads();
@@ -668,19 +739,19 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
   }
   // G_b[i][j] = sum_v w_i(v) conj(w_j(v)), w_i = Gamma_L^1/2 (kept planes of RIGHT run i)
   for (int i = 0; i < sr; ++i) {
-    const double2* wi = wcol(i);
+    const V* wi = wcol(i);
     for (int j0 = i; j0 < sr; j0 += kGnChunk) {
       double v[2 * kGnChunk];
 #pragma unroll
       for (int k = 0; k < 2 * kGnChunk; ++k) v[k] = 0.0;
       for (long long u = threadIdx.x; u < nL; u += blockDim.x) {
         const double g = a.gl[a.lplanes[u / a.nxy]];
-        const double2 x = wi[u];
+        const double2 x = vload(wi, u);
 #pragma unroll
         for (int k = 0; k < kGnChunk; ++k) {
           const int j = j0 + k;
           if (j < sr) {
-            const double2 w = wcol(j)[u];
+            const double2 w = vload(wcol(j), u);
             v[2 * k] += g * (x.x * w.x + x.y * w.y);
             v[2 * k + 1] += g * (x.y * w.x - x.x * w.y);
           }
@@ -789,6 +860,39 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
   }
 }
 
+// double -> double-float copies of the operator tables
+__global__ void k_real_to_df(const double* x, float2* y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const df d = df_split(x[i]);
+    y[i] = make_float2(d.hi, d.lo);
+  }
+}
+__global__ void k_cplx_to_df(const double2* x, float4* y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = dfc_from_double2(x[i]);
+}
+
+template <int R>
+cudaError_t stencil_df_r(dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a, bool prepare) {
+  if (prepare) return cudaFuncSetAttribute(k_stencil_df<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_stencil_df<R><<<grid, threads, smem, s>>>(a);
+  return cudaSuccess;
+}
+
+// prepare = true sets the kernel's shared-memory limit; false launches it
+cudaError_t stencil_df(int R, dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a,
+                       bool prepare) {
+  switch (R) {
+    case 1: return stencil_df_r<1>(grid, threads, smem, s, a, prepare);
+    case 2: return stencil_df_r<2>(grid, threads, smem, s, a, prepare);
+    case 3: return stencil_df_r<3>(grid, threads, smem, s, a, prepare);
+    case 4: return stencil_df_r<4>(grid, threads, smem, s, a, prepare);
+    case 5: return stencil_df_r<5>(grid, threads, smem, s, a, prepare);
+    case 6: return stencil_df_r<6>(grid, threads, smem, s, a, prepare);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 // ---------------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------------
@@ -845,6 +949,7 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
               int** d_res_it, int** d_res_st) {
   SweepBufs& B = *ctx->sweep;
   const Geometry& g = ctx->g;
+  const bool dfm = ctx->opts.precision == TRANSEC_PREC_DF64;  // double-float kernels
   const int ne = (int)energies.size();
   const int nitems = (int)items.size();
   const long long n = g.n, nxy = g.nxy;
@@ -871,6 +976,7 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   B.cap_rho = std::max(B.cap_rho, (size_t)S * nblk3 * 4);
   MS_CK(grow(B.slots, B.cap_slots, (size_t)S));
   MS_CK(grow(B.ms, B.cap_slots, (size_t)S));
+  MS_CK(grow(B.escale, B.cap_slots, (size_t)S));
   B.cap_slots = std::max(B.cap_slots, (size_t)S);
   MS_CK(grow(B.sh, B.cap_shs, (size_t)S * ne));
   MS_CK(grow(B.coef, B.cap_shs, (size_t)S * ne));
@@ -883,7 +989,13 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   B.cap_rnd = std::max(B.cap_rnd, need_rnd);
   MS_CK(grow(B.lrank, B.cap_nz, (size_t)g.nz));
   MS_CK(grow(B.rrank, B.cap_nz, (size_t)g.nz));
+  MS_CK(grow(B.gam_df, B.cap_nz, (size_t)g.nz));
   B.cap_nz = std::max(B.cap_nz, (size_t)g.nz);
+  MS_CK(grow(B.v_df, B.cap_n, (size_t)n));
+  B.cap_n = std::max(B.cap_n, (size_t)n);
+  const size_t nph = (size_t)ctx->nk * 2 * 2 * kPhaseN;
+  MS_CK(grow(B.phase_df, B.cap_ph, nph));
+  B.cap_ph = std::max(B.cap_ph, nph);
   if (!B.queue) MS_CK(cudaMalloc(&B.queue, sizeof(Queue)));
   B.S = S; B.ne = ne; B.n = n; B.no = no; B.nblk_st = nblk_st; B.nblk3 = nblk3; B.nitems = nitems;
   B.nrnd = nrep;
@@ -893,6 +1005,12 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   for (int i = 0; i < nrp; ++i) rr[ctx->rplanes[i]] = i;
   MS_CK(cudaMemcpyAsync(B.lrank, lr.data(), g.nz * sizeof(int), cudaMemcpyHostToDevice, st));
   MS_CK(cudaMemcpyAsync(B.rrank, rr.data(), g.nz * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (dfm) {
+    k_real_to_df<<<256, 256, 0, st>>>(ctx->d_v, B.v_df, n);
+    k_real_to_df<<<1, 256, 0, st>>>(ctx->d_gam, B.gam_df, g.nz);
+    k_cplx_to_df<<<1, 256, 0, st>>>(ctx->d_phase, B.phase_df, (long long)nph);
+    ctx->launches += 3;
+  }
   MS_CK(cudaMemcpyAsync(B.items, items.data(), nitems * sizeof(MsItem), cudaMemcpyHostToDevice, st));
   MS_CK(cudaMemcpyAsync(B.energies, energies.data(), ne * sizeof(double), cudaMemcpyHostToDevice, st));
   Queue q0{};
@@ -921,10 +1039,26 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   a.n = n; a.no = no; a.nxy = nxy; a.lplanes = ctx->d_lplanes; a.rplanes = ctx->d_rplanes;
   a.lrank = B.lrank; a.rrank = B.rrank; a.nlp = nlp; a.nrp = nrp; a.gl = ctx->d_gl; a.gr = ctx->d_gr;
   a.rho_part = B.rho_part; a.nblk3 = nblk3; a.sig_part = B.sig_part; a.nblk_st = nblk_st;
-  a.tol = ctx->opts.tol; a.maxit = ctx->opts.maxit;
+  a.tol = ctx->opts.tol; a.maxit = ctx->opts.maxit; a.escale = B.escale;
   a.res_t = res_t; a.res_it = res_it; a.res_st = res_st;
 
-  MS_CK(prepare_stencil<double>(g.R, ts.smem));
+  if (dfm) MS_CK(stencil_df(g.R, dim3(1), 0, ts.smem, st, StencilDfArgs{}, true));
+  else MS_CK(prepare_stencil<double>(g.R, ts.smem));
+  StencilDfArgs da{};
+  da.r = reinterpret_cast<const float4*>(B.R); da.q = reinterpret_cast<float4*>(B.Q); da.part = B.sig_part;
+  da.slots = B.slots; da.escale = B.escale; da.phase = B.phase_df; da.v = B.v_df; da.gam = B.gam_df;
+  for (int m = 0; m <= kMaxR; ++m) {
+    const df x = df_split(g.kx[m]), y = df_split(g.ky[m]), z = df_split(g.kz[m]);
+    da.kx[m] = make_float2(x.hi, x.lo);
+    da.ky[m] = make_float2(y.hi, y.lo);
+    da.kz[m] = make_float2(z.hi, z.lo);
+  }
+  da.diag_c = g.diag_c; da.nx = g.nx; da.ny = g.ny; da.nz = g.nz; da.nxy = g.nxy; da.n = g.n; da.H = 2;
+  da.TX = ts.TX; da.TY = ts.TY; da.D = ts.D; da.ntx = ts.ntx; da.conj = 0; da.slot_stride = 2 * n;
+  UpdateDfArgs dua{};
+  dua.r = reinterpret_cast<float4*>(B.R); dua.q = reinterpret_cast<const float4*>(B.Q); dua.sig_part = B.sig_part;
+  dua.sig_nblk = nblk_st; dua.rho_part = B.rho_part; dua.slots = B.slots; dua.escale = B.escale; dua.n = n;
+  dua.slot_stride = 2 * n; dua.H = 2;
   StencilArgs<double> sa{};
   sa.r = B.R; sa.q = B.Q; sa.part = B.sig_part; sa.slots = B.slots; sa.phase = ctx->d_phase;
   sa.v = ctx->d_v; sa.gam = ctx->d_gam; sa.g = g; sa.H = 2; sa.TX = ts.TX; sa.TY = ts.TY; sa.D = ts.D;
@@ -939,10 +1073,16 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   const dim3 igrid((unsigned)std::min<long long>((n + 255) / 256, 1024), (unsigned)S);
   const dim3 isgrid((unsigned)std::min<long long>((2 * no + 255) / 256, 256), (unsigned)ne, (unsigned)S);
 
-  k_ms_assign<<<1, 32, 0, st>>>(a);
-  k_ms_init<<<igrid, 256, 0, st>>>(a);
-  k_ms_init_shift<<<isgrid, 256, 0, st>>>(a);
-  k_ms_rho0<<<S, 256, 0, st>>>(a);
+  // the queue's refill stage: assignment, vectors, per-shift state, rho_0
+  auto refill = [&]() {
+    k_ms_assign<<<1, 32, 0, st>>>(a);
+    if (dfm) k_ms_init<float4><<<igrid, 256, 0, st>>>(a);
+    else k_ms_init<double2><<<igrid, 256, 0, st>>>(a);
+    k_ms_init_shift<<<isgrid, 256, 0, st>>>(a);
+    if (dfm) k_ms_rho0<float4><<<S, 256, 0, st>>>(a);
+    else k_ms_rho0<double2><<<S, 256, 0, st>>>(a);
+  };
+  refill();
   MS_CK(cudaGetLastError());
   ctx->launches += 4;
 
@@ -983,23 +1123,26 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   for (int i = 0; i < C; ++i) {
     sa.p_in = (i % 2 == 0) ? B.P0 : B.P1;
     sa.p_out = (i % 2 == 0) ? B.P1 : B.P0;
+    da.p_in = reinterpret_cast<const float4*>(sa.p_in);
+    da.p_out = reinterpret_cast<float4*>(sa.p_out);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 0], st, cudaEventRecordExternal);
-    launch_stencil<double>(g.R, sgrid, ts.threads, ts.smem, st, sa);
+    if (dfm) stencil_df(g.R, sgrid, ts.threads, ts.smem, st, da, false);
+    else launch_stencil<double>(g.R, sgrid, ts.threads, ts.smem, st, sa);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 1], st, cudaEventRecordExternal);
     k_ms_coef<<<S, 256, 0, st>>>(a);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 2], st, cudaEventRecordExternal);
-    k_ms_shift<<<shgrid, 256, 0, st>>>(a);
+    if (dfm) k_ms_shift_df<<<shgrid, 256, 0, st>>>(a);
+    else k_ms_shift<<<shgrid, 256, 0, st>>>(a);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 3], st, cudaEventRecordExternal);
     ua.p = sa.p_out;
-    k_update<double><<<ugrid, 256, 0, st>>>(ua);
+    if (dfm) k_update_df<<<ugrid, 256, 0, st>>>(dua);
+    else k_update<double><<<ugrid, 256, 0, st>>>(ua);
     k_ms_scalars<<<S, 256, 0, st>>>(a);
   }
-  k_ms_trace<<<dim3((unsigned)ne, (unsigned)S), 256, 0, st>>>(a);
+  if (dfm) k_ms_trace<float4><<<dim3((unsigned)ne, (unsigned)S), 256, 0, st>>>(a);
+  else k_ms_trace<double2><<<dim3((unsigned)ne, (unsigned)S), 256, 0, st>>>(a);
   k_ms_release<<<1, 32, 0, st>>>(a);
-  k_ms_assign<<<1, 32, 0, st>>>(a);
-  k_ms_init<<<igrid, 256, 0, st>>>(a);
-  k_ms_init_shift<<<isgrid, 256, 0, st>>>(a);
-  k_ms_rho0<<<S, 256, 0, st>>>(a);
+  refill();
   if (device_loop) {
     k_continue<<<1, 1, 0, st>>>(loop, B.queue);
   } else {
@@ -1220,7 +1363,10 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_rs, run_slot.data(), run_slot.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->s);
   const size_t smem = (size_t)(kGnMaxR * kGnMaxL + kGnMaxR * kGnMaxR) * sizeof(double2);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ms_gn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool dfm = ctx->opts.precision == TRANSEC_PREC_DF64;
+  if (e == cudaSuccess)
+    e = dfm ? cudaFuncSetAttribute(k_ms_gn<float4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+            : cudaFuncSetAttribute(k_ms_gn<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaEvent_t g0 = nullptr, g1 = nullptr;
   const bool prof = ctx->opts.profile != 0;
   if (e == cudaSuccess && prof) {
@@ -1235,7 +1381,8 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
     ga.lplanes = ctx->d_lplanes; ga.rplanes = ctx->d_rplanes; ga.nlp = (int)ctx->lplanes.size();
     ga.nrp = (int)ctx->rplanes.size(); ga.gl = ctx->d_gl; ga.gr = ctx->d_gr; ga.T = d_T; ga.rank = d_rank;
     ga.status = d_st; ga.drop = 1e-13;
-    k_ms_gn<<<dim3((unsigned)ne, (unsigned)nrep, 2), 256, smem, ctx->s>>>(ga);
+    if (dfm) k_ms_gn<float4><<<dim3((unsigned)ne, (unsigned)nrep, 2), 256, smem, ctx->s>>>(ga);
+    else k_ms_gn<double2><<<dim3((unsigned)ne, (unsigned)nrep, 2), 256, smem, ctx->s>>>(ga);
     ctx->launches += 1;
     e = cudaGetLastError();
   }

@@ -8,6 +8,9 @@
 * transec_transmission_sketch: the full trace T(E, k) = 4 Tr[Gamma_L G^dagger Gamma_R G]
   from random left and right right-hand sides, against the dense-LU full trace over
   every left-CAP column, at k and -k, within |dT| <= 1e-6 (the metric's bar).
+
+Both arithmetics of the engine are covered: FP64 (precision 0) and double-float
+(precision 2: vectors and the stencil, vector and per-shift updates in pairs of floats).
 """
 
 import numpy as np
@@ -32,7 +35,11 @@ def _dense_cols(inst, e, kf, cols):
     return transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf, cols)[1]
 
 
-def test_shifted_columns_match_dense_lu_at_both_k():
+PRECISIONS = [0, 2]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_shifted_columns_match_dense_lu_at_both_k(precision):
     need_gpu()
     kf = (0.21, -0.34)
     inst = _inst(kf)
@@ -40,7 +47,7 @@ def test_shifted_columns_match_dense_lu_at_both_k():
     energies = np.linspace(0.12, 0.78, 9)
     sup = left_support(g, inst.gamma_l)
     cols = np.array([0, 17, 101, 239], np.int64)
-    with context(inst) as tr:
+    with context(inst, precision=precision) as tr:
         r = tr.shifted_columns(energies, np.zeros(cols.size, np.int32), cols)
     assert np.all(r["status"] == 0), r["status"]
     for s, e in enumerate(energies):
@@ -52,18 +59,19 @@ def test_shifted_columns_match_dense_lu_at_both_k():
     assert np.all(r["iters"] > 0) and np.all(r["iters"].max(axis=1) >= r["iters"].min(axis=1))
 
 
-def test_shifted_columns_agree_with_separate_solves_and_refill():
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_shifted_columns_agree_with_separate_solves_and_refill(precision):
     need_gpu()
     kf = (0.4375, 0.1875)
     inst = _inst(kf, seed=9, nx=5, ny=6, nz=36, order=12, ncap=7)
     energies = np.array([0.2, 0.35, 0.5, 0.65])
     cols = np.array([3, 44, 90, 131, 170], np.int64)
     ik = np.zeros(cols.size, np.int32)
-    with context(inst, tol=1e-11) as tr:
+    with context(inst, tol=1e-11, precision=precision) as tr:
         all_in = tr.shifted_columns(energies, ik, cols)
         tr.set_solver(slots=2)  # five runs through two slots: retire and refill on the GPU
         refill = tr.shifted_columns(energies, ik, cols)
-        tr.set_solver(slots=0)
+        tr.set_solver(slots=0, precision=0)
         sep = [tr.column_contributions(np.full(cols.size, e), ik, cols) for e in energies]
     assert np.all(all_in["status"] == 0) and np.all(refill["status"] == 0)
     np.testing.assert_array_equal(all_in["t"], refill["t"])
@@ -73,13 +81,14 @@ def test_shifted_columns_agree_with_separate_solves_and_refill():
         assert np.abs(all_in["t_minus"][:, s] - sep[s]["t_minus"]).max() <= 1e-9
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("kf,order", [((0.23, -0.37), 8), ((0.0, 0.0), 4), ((0.4375, 0.3125), 12)])
-def test_sketch_full_trace_matches_dense_lu(kf, order):
+def test_sketch_full_trace_matches_dense_lu(kf, order, precision):
     need_gpu()
     inst = _inst(kf, seed=13, nx=6, ny=6, nz=44, order=order, ncap=9)
     g = inst.grid
     energies = np.linspace(0.1, 0.9, 7)
-    with context(inst) as tr:
+    with context(inst, precision=precision) as tr:
         r = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=3)
     assert np.all(r["status"] == 0), r["status"]
     for s, e in enumerate(energies):
