@@ -4,14 +4,20 @@
 Workload: bulk fcc Cu along [001], a = 6.82 bohr, 20x20x480 grid (h = 0.341 bohr),
 order-12 stencil, Gaussian-atom potential with +-2% jitter, 64-plane quadratic CAPs
 of peak 0.3 Ha, 8x8 Monkhorst-Pack k-mesh, 256 energies in E_F +- 0.3 Ha; solver
-residual 1e-10.  One (E, k) needs n_rhs = 25,600 column solves (every left-CAP grid
-point), each thousands of Krylov iterations, so a step is a seeded sample of
-(E, k, column) items, each solved to convergence, traced and summed (the whole hot
-path: right-hand side, stencil, Krylov updates, retirement, trace).  With the
-transpose BiCG every column also yields the (E, -k) column, and the mesh holds both
-k and -k, so
+residual 1e-10.
 
-    value = (E,k)-equivalent solves/s = 2 * column-solves/s / n_rhs.
+Default form (--form sketch): a step is the full trace T(E, k) and T(E, -k) of one
+seeded k-pair of the mesh at a window of 16 consecutive energies of the 256 (seeded
+position), from a two-sided randomized sketch of Gamma_R^1/2 G Gamma_L^1/2 (12 runs
+with random left-CAP right-hand sides, 24 with random right-CAP ones), every run a
+multi-shift transpose BiCG over the window in double-float arithmetic: the whole hot
+path (operator, right-hand sides, stencil, Krylov and per-shift updates, convergence,
+retirement, the trace reduction) on the GPU.  value = (E, k) values per second = 32 per
+step / step time.
+
+--form fp64 / mixed: the plain engine on seeded (E, k, column) samples, each column
+solved to convergence; value = 2 * column-solves/s / n_rhs (each column gives the k
+and -k columns).  --form columns: the multi-shift engine on sampled unit columns.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle instead.
 """
@@ -47,6 +53,12 @@ HBM_FALLBACK_GBS = 6800.0
 FP64_STENCIL_DRAM_PER_POINT_HALF = 900.5e6 / 12.288e6
 # FP64 ALU roofline: 2 FP64 FMA per clock per SM x 152 SMs x 2070 MHz x 2 flops
 FP64_PEAK_TFLOPS = 2 * 152 * 2.070e9 * 2 / 1e12
+# FP32 pipe roofline of the double-float stencil, in FP32 operations (add, multiply or
+# FMA, one each): 128 FP32 lanes per SM x 152 SMs x 2070 MHz
+FP32_OPS_PEAK_T = 128 * 152 * 2.070e9 / 1e12
+# DRAM bytes per point-half of one double-float stencil launch (ncu capture in
+# profiles/k_stencil_df_cu_bulk.md); None until captured for the current kernel
+DF_STENCIL_DRAM_PER_POINT_HALF = None
 
 
 def stencil_flops_per_point(order: int) -> int:
@@ -54,6 +66,16 @@ def stencil_flops_per_point(order: int) -> int:
     p = r + beta p (8), diagonal term (6), 3 axes x R neighbour pairs x (pair add 2,
     weight 2, accumulate 2) = 18R, pairing dot (8)."""
     return 18 * (order // 2) + 22
+
+
+def stencil_df_ops_per_point(order: int) -> int:
+    """FP32 operations of the double-float stencil per grid point and half, counted
+    from its algorithm (halo recomputation excluded): p = r + beta p (complex
+    double-float multiply 38 + accurate add 2 x 20 = 78), diagonal term (accurate
+    subtraction 20, four products 16, four accumulations 32 = 68), per neighbour pair
+    and axis and component 20 (TwoSum pair 8, product 4, accumulation 8) = 120 R,
+    combining the axes 54, pairing dot with its scaling 56."""
+    return 78 + 68 + 120 * (order // 2) + 54 + 56
 
 
 def stencil_bytes_per_point(elem: int) -> int:
@@ -346,6 +368,219 @@ def run_uneven_batch(args):
     return 0
 
 
+SKETCH_WINDOW, SKETCH_LEFT, SKETCH_RIGHT = 16, 12, 24
+
+
+def sketch_plan(n_energy: int, reps, count: int, window: int, seed: int = 3000):
+    """(k index, first energy index) of each sketch step: a seeded k-pair
+    representative and a seeded window position, drawn independently per step."""
+    rng = np.random.default_rng(seed)
+    ks = np.asarray(reps, np.int64)[rng.integers(0, len(reps), count)]
+    starts = rng.integers(0, n_energy - window + 1, count)
+    return [(int(k), int(e)) for k, e in zip(ks, starts)]
+
+
+def run_sketch(args):
+    """Full-trace T(E, +-k) over energy windows by the two-sided sketch (default form)."""
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from workloads import cu_bulk, rh_point_contact
+    import paper_2208_02783_gb300 as pkg
+    from paper_2208_02783_gb300 import build, replicas
+
+    pkg.load(build.build())
+    rh = args.workload == "rh_point_contact"
+    inst = rh_point_contact() if rh else cu_bulk()
+    g = inst.grid
+    reps = k_representatives(inst.kfrac)
+    W, sl, sr = args.window, args.s_left, args.s_right
+    prec = pkg.PREC_FP64 if args.form == "sketch_fp64" else pkg.PREC_DF64
+    tr = pkg.Transec.from_instance(inst, device=local, tol=1e-10, precision=prec)
+    e2e_steps = min(args.steps, 2)
+    plan = sketch_plan(len(inst.energies), reps, (args.warmup + args.steps + e2e_steps) * ws, W)
+
+    def window(i):
+        k, e0 = plan[i * ws + rank]
+        return k, inst.energies[e0:e0 + W].astype(np.float64)
+
+    def step(i):
+        k, en = window(i)
+        return tr.transmission_sketch(en, [k], s_left=sl, s_right=sr, seed=1000 + i)
+
+    if args.profile_case:
+        # bounded case for the profilers: one window, 40 iterations (the shifts stop as
+        # not converged), host-driven chunk graphs (profilers do not enter graphs with
+        # conditional nodes); about 2 GB on the device
+        tr.set_solver(maxit=40, host_loop=1)
+        step(0)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "ok", "workload": args.workload, "form": "sketch"}))
+        tr.close()
+        return 0
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    tr.stats_reset()
+    clocks = Clocks(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks.start()
+    ev0.record()
+    results = [step(args.warmup + i) for i in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    ms = replicas.max_over_ranks(ev0.elapsed_time(ev1), device=dev)
+    st = tr.stats()
+    sw = tr.sweep_stats()
+    per_step = 2 * W  # T(E, k) and T(E, -k) for every energy of the window
+    value = replicas.whole_job_rate(per_step * args.steps, ws, ms / 1e3)
+    T = np.concatenate([r["T"][0] for r in results])
+    Tm = np.concatenate([r["T_minus"][0] for r in results])
+    status = np.concatenate([r["status"][0] for r in results])
+    its = np.concatenate([r["iters"][0] for r in results])
+    ok = status == 0
+    pm_diff = float(np.abs(T[ok] - Tm[ok]).max()) if ok.any() else None
+
+    # end to end through the public API with host arrays: the window's energies and k in,
+    # T(E, +-k), ranks, statuses and iterations out, host wall clock
+    e2e_s = 0.0
+    for i in range(e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(args.warmup + args.steps + i)
+        e2e_s += time.perf_counter() - t0
+    e2e_s = replicas.max_over_ranks(e2e_s, device=dev)
+    e2e_value = replicas.whole_job_rate(per_step * e2e_steps, ws, e2e_s)
+
+    # parity against the plain FP64 arithmetic on the first timed window: the same sketch
+    # in the FP64 engine (the double-float form's metric bar is |dT| <= 1e-6 vs FP64)
+    parity = None
+    if rank == 0 and prec == pkg.PREC_DF64 and not args.no_parity:
+        k, en = window(args.warmup)
+        tr.set_solver(precision=pkg.PREC_FP64)
+        ref = tr.transmission_sketch(en, [k], s_left=sl, s_right=sr, seed=1000 + args.warmup)
+        tr.set_solver(precision=prec)
+        got = results[0]
+        okp = (ref["status"][0] == 0) & (got["status"][0] == 0)
+        parity = {"window_energies": W, "k_index": k,
+                  "max_abs_dT_vs_fp64": float(np.abs(got["T"][0][okp] - ref["T"][0][okp]).max()),
+                  "max_abs_dT_minus_vs_fp64": float(np.abs(got["T_minus"][0][okp] - ref["T_minus"][0][okp]).max()),
+                  "fp64_all_converged": bool(np.all(ref["status"] == 0))}
+
+    # profiled pass (separate from the timed steps): one window for 200 iterations with
+    # every shift of every run active, each stencil and shift-update launch bracketed by
+    # CUDA events on the context's stream
+    prof_its = 200
+    k, en = window(0)
+    tr.set_solver(profile=1, maxit=prof_its)
+    tr.stats_reset()
+    tr.transmission_sketch(en, [k], s_left=sl, s_right=sr, seed=1)
+    swp = tr.sweep_stats()
+    tr.set_solver(profile=0, maxit=100000)
+    runs = sl + sr
+    ph_per_launch = runs * 2 * g.n  # every run active: both halves of every grid point
+    st_ms = swp["stencil_ms"] / max(1, swp["stencil_launches"])
+    sh_ms = swp["shift_ms"] / max(1, swp["shift_launches"])
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    if prec == pkg.PREC_DF64:
+        ops = stencil_df_ops_per_point(g.order) * ph_per_launch
+        achieved = ops / (st_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_OPS_PEAK_T, "unit": "T FP32-op/s",
+                "frac": achieved / FP32_OPS_PEAK_T,
+                "traffic": (DF_STENCIL_DRAM_PER_POINT_HALF * ph_per_launch
+                            if DF_STENCIL_DRAM_PER_POINT_HALF and not rh else None),
+                "kernel": f"k_stencil_df<{g.order // 2}> (double-float stencil fused with p = r + beta p and the "
+                          "pairing dot)",
+                "per_launch": {"point_halves": ph_per_launch, "fp32_ops": ops, "ms": st_ms,
+                               "fp64_equivalent_tflops": stencil_flops_per_point(g.order) * ph_per_launch / (st_ms / 1e3) / 1e12,
+                               "hbm_gbs": stencil_bytes_per_point(16) * ph_per_launch / (st_ms / 1e3) / 1e9},
+                "peak_source": "derived: 128 FP32 lanes/SM x 152 SMs x 2070 MHz (one add, multiply or FMA "
+                               "per lane and clock)",
+                "fp64_equivalent_frac_of_fp64_peak": stencil_flops_per_point(g.order) * ph_per_launch
+                / (st_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS}
+    else:
+        flops = stencil_flops_per_point(g.order) * ph_per_launch
+        achieved = flops / (st_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": f"k_stencil<double,{g.order // 2}>",
+                "per_launch": {"point_halves": ph_per_launch, "flops": flops, "ms": st_ms},
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
+    no = max(int(np.count_nonzero(inst.gamma_l)), int(np.count_nonzero(inst.gamma_r))) * g.nxy
+    shift_bytes = runs * W * 2 * no * 64  # read/write p_sigma and x_sigma, 16 B each, per shift and half
+    roof["shift_kernel"] = {"ms": sh_ms, "bytes_per_launch": shift_bytes,
+                            "hbm_gbs": shift_bytes / (sh_ms / 1e3) / 1e9,
+                            "hbm_frac_of_measured": shift_bytes / (sh_ms / 1e3) / 1e9 / hbm_peak}
+    roof["timing"] = (f"separate profiled pass: one window, {runs} runs x {W} shifts, {prof_its} iterations, "
+                      "CUDA events around every stencil and shift-update launch on the context's stream")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "df64+f64" if prec == pkg.PREC_DF64 else "c128",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD_RH if rh else WORKLOAD,
+            "form": ("full trace T(E, +-k) from a two-sided randomized sketch of Gamma_R^1/2 G Gamma_L^1/2: "
+                     f"{sl} left + {sr} right random right-hand sides, each a multi-shift transpose BiCG over "
+                     f"a window of {W} energies, " + ("double-float vectors and stencil, FP64 scalars"
+                                                      if prec == pkg.PREC_DF64 else "FP64")),
+            "step": f"one seeded k-pair x {W} consecutive energies (seeded position) = {per_step} (E, k) values",
+            "value_derivation": f"{per_step} (E, k) values per step / step time (T(E, k) and T(E, -k) are "
+                                "estimated from independent halves of the runs)",
+            "mean_seed_iterations": float(its.mean()), "max_seed_iterations": int(its.max()),
+            "failed_results": int((~ok).sum()), "max_abs_T_k_minus_T_mk": pm_diff,
+            "min_rank": int(np.concatenate([r["rank"][0] for r in results]).min()),
+            "parity_vs_fp64": parity,
+            "l2": "per-step working set (36 runs x 2 halves x 192,000 points x 4 vectors x 16 B = 0.9 GB, plus "
+                  "the per-shift planes) exceeds L2; no flush needed",
+            "sampling": "steps draw (k-pair, window position) from a seeded generator; ranks take disjoint steps",
+        },
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": W * 8 + 4,
+                "d2h_bytes_per_step": W * (8 + 8 + 4 + 4 + 4)},
+        "gpu_launches": int(st["launches"]),
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        mean_its = golden_mean_iterations()
+        items = draw_items(inst, reps, inst.n_rhs, 64, 7000)
+        with OraclePool("rh_point_contact" if rh else "cu_bulk") as op:
+            op.rate(inst, items, mean_its, budget_s=1.0)  # operators built, caches warm
+            crate, n_it, dt = op.rate(inst, items, mean_its, budget_s=12.0)
+            procs = op.procs
+        line["cpu_baseline"] = {
+            "value": 2.0 * crate / inst.n_rhs, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": (f"oracle transpose BiCG (numpy/scipy complex128), one single-threaded process per core "
+                       f"({procs}), each on its own seeded left-CAP column of the workload for {n_it} iterations "
+                       f"(median; {dt:.1f} s wall); column time = time per iteration x {mean_its:.0f} (oracle "
+                       f"mean iterations to 1e-10 over the committed golden columns); (E, k) rate = 2 x "
+                       f"column rate / {inst.n_rhs} columns (the oracle's T(E, k) is the sum over every "
+                       "left-CAP column, each giving the k and -k columns)"),
+        }
+    if rank == 0:
+        print(json.dumps(line))
+    tr.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 UNET_LAYERS = [(4, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 64, 2),
                (96, 32, 1), (32, 32, 1), (48, 16, 0), (16, 16, 0), (16, 2, 0)]  # (cin, cout, level)
 
@@ -479,7 +714,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--form", default="sketch", choices=["sketch", "sketch_fp64", "fp64", "mixed"],
+                    help="sketch: full trace from the two-sided sketch (double-float); sketch_fp64: the "
+                         "same in FP64; fp64 / mixed: the plain engine on sampled columns")
+    ap.add_argument("--window", type=int, default=SKETCH_WINDOW, help="energies per sketch step")
+    ap.add_argument("--s-left", type=int, default=SKETCH_LEFT)
+    ap.add_argument("--s-right", type=int, default=SKETCH_RIGHT)
+    ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--slots", type=int, default=0)
     ap.add_argument("--items", type=int, default=0, help="column solves per step and GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -498,6 +739,8 @@ def main():
         return run_uneven_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.form in ("sketch", "sketch_fp64"):
+        return run_sketch(args)
 
     import torch
     import torch.distributed as dist

@@ -41,10 +41,15 @@ __device__ inline df fast_two_sum(float a, float b) {
 
 __device__ inline df df_norm(df a) { return fast_two_sum(a.hi, a.lo); }
 
-// a + b (the "sloppy" double-word sum: error ~ 2^-46 (|a| + |b|))
+// a + b with the error bounded relative to the result, |err| <= 3u^2 |a + b| (u = 2^-24;
+// Joldes, Muller & Popescu, ACM TOMS 44 (2017), the accurate double-word sum): the
+// Krylov updates r - alpha q and r + beta p cancel as the residual falls, and a sum
+// whose error scales with |a| + |b| instead costs the solver iterations
 __device__ inline df df_add(df a, df b) {
   const df s = two_sum(a.hi, b.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+  const df t = two_sum(a.lo, b.lo);
+  const df v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
 }
 __device__ inline df df_neg(df a) { return df{-a.hi, -a.lo}; }
 __device__ inline df df_sub(df a, df b) { return df_add(a, df_neg(b)); }

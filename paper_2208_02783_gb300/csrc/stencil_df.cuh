@@ -53,8 +53,16 @@ __device__ inline df df_pair(df a, df b) {
 
 __device__ inline df acc_df(const dfacc& a) { return df{a.hi, a.lo}; }
 
+// Shared memory of one stencil block: the centre plane of each half with its lateral
+// halo, then a ring of the 2R+1 planes around it for every thread's own column (the
+// z-neighbours; only the owning thread reads and writes its column, so the ring needs
+// no barrier).  Kept out of registers, the ring lets two blocks share an SM.
+__host__ __device__ inline size_t stencil_df_smem(int R, int TX, int TY, int H, int threads) {
+  return (size_t)H * (TX + 2 * R) * (TY + 2 * R) * sizeof(float4) + (size_t)(2 * R + 1) * threads * sizeof(float4);
+}
+
 template <int R>
-__global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 2) k_stencil_df(const StencilDfArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2][32];
   float4* sm = reinterpret_cast<float4*>(smem_raw);
@@ -85,6 +93,8 @@ __global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArg
   const int SW = TX + 2 * R;
   const int SHt = TY + 2 * R;
   float4* my = sm + half * SW * SHt;
+  float4* ring = sm + a.H * SW * SHt + t;  // this thread's column, stride blockDim.x
+  const int rs = blockDim.x;
   const long long base = (long long)slot * a.slot_stride + (long long)half * a.n;
   const float4* __restrict__ r = a.r + base;
   const float4* __restrict__ pin = a.p_in + base;
@@ -105,27 +115,45 @@ __global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArg
     if (wy) v = dfc_mul(v, dfc_load(ph[kPhaseN + kPhaseW + wy]));
     return v;
   };
+  // ring position of plane z (planes z0 - R .. z1 + R - 1 cycle through 2R + 1 slots)
+  auto rpos = [&](int z) { return (z - z0 + R) % (2 * R + 1); };
 
-  dfc qv[2 * R + 1];
-  qv[0] = dfc_zero();
-#pragma unroll
-  for (int m = 1; m <= 2 * R; ++m) {
-    const int z = z0 - R + m - 1;
-    qv[m] = (inside && z >= 0 && z < nz) ? pnew((long long)z * nxy + pidx) : dfc_zero();
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int z = z0 - R; z < z0 + R; ++z)
+    ring[rpos(z) * rs] = (inside && z >= 0 && z < nz) ? dfc_store(pnew((long long)z * nxy + pidx)) : zero4;
+  // the loads of the plane that enters the ring next are issued one plane ahead
+  float4 nr = zero4, np = zero4, nv = zero4;
+  if (inside && z0 + R < nz) {
+    nr = r[(long long)(z0 + R) * nxy + pidx];
+    np = pin[(long long)(z0 + R) * nxy + pidx];
   }
+  // a tile as wide as the cell (one wrap at most) takes its x-halo from its own
+  // points: the cell at x + nx is exp(i k L_a) p(x), the cell at x - nx is exp(-i k L_a) p(x)
+  const bool xself = TX == nx && nx >= R;
 
   dfacc sg_re, sg_im;
   const int nh = 2 * R * (TX + TY);
+  const int h0 = xself ? 2 * R * TY : 0;  // first halo cell computed from global memory
   for (int zc = z0; zc < z1; ++zc) {
-#pragma unroll
-    for (int m = 0; m < 2 * R; ++m) qv[m] = qv[m + 1];
     {
       const int z = zc + R;
-      qv[2 * R] = (inside && z < nz) ? pnew((long long)z * nxy + pidx) : dfc_zero();
+      ring[rpos(z) * rs] = (inside && z < nz) ? dfc_store(dfc_fma(beta, dfc_load(np), dfc_load(nr))) : zero4;
+      if (inside && z + 1 < nz) {
+        nr = r[(long long)(z + 1) * nxy + pidx];
+        np = pin[(long long)(z + 1) * nxy + pidx];
+      }
     }
-    const dfc c = qv[R];
+    const dfc c = dfc_load(ring[rpos(zc) * rs]);
+    if (inside) {
+      const float2 vv = a.v[(long long)zc * nxy + pidx];
+      nv = make_float4(vv.x, vv.y, 0.f, 0.f);
+    }
     if (worker) my[(ty + R) * SW + tx + R] = dfc_store(inside ? c : wrapped(gx, gy, zc));
-    for (int h = worker ? lt : nh; h < nh; h += npt) {
+    if (xself && inside) {
+      if (tx < R) my[(ty + R) * SW + tx + R + nx] = dfc_store(dfc_mul(c, dfc_load(ph[kPhaseW + 1])));
+      if (tx >= nx - R) my[(ty + R) * SW + tx + R - nx] = dfc_store(dfc_mul(c, dfc_load(ph[kPhaseW - 1])));
+    }
+    for (int h = worker ? h0 + lt : nh; h < nh; h += npt) {
       int hx, hy;
       if (h < 2 * R * TY) {
         const int row = h / (2 * R), k = h - row * 2 * R;
@@ -142,8 +170,7 @@ __global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArg
     __syncthreads();
     if (inside) {
       const long long off = (long long)zc * nxy + pidx;
-      const float2 vv = a.v[off];
-      const df dr = df_sub(ediag, df{vv.x, vv.y});
+      const df dr = df_sub(ediag, df{nv.x, nv.y});
       const float2 gg = a.gam[zc];
       const df di = df{gg.x, gg.y};
       // per-axis accumulators keep independent dependency chains
@@ -156,15 +183,15 @@ __global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArg
 #pragma unroll
       for (int m = 1; m <= R; ++m) {
         const float4 xa = ctr[m], xb = ctr[-m], ya = ctr[m * SW], yb = ctr[-m * SW];
-        const dfc za = qv[R + m], zb = qv[R - m];
+        const float4 za = ring[rpos(zc + m) * rs], zb = ring[rpos(zc - m + 2 * R + 1) * rs];
         const df ckx = df{a.kx[m].x, a.kx[m].y}, cky = df{a.ky[m].x, a.ky[m].y},
                  ckz = df{a.kz[m].x, a.kz[m].y};
         xre.add(df_mul_raw(df_pair(df{xa.x, xa.y}, df{xb.x, xb.y}), ckx));
         xim.add(df_mul_raw(df_pair(df{xa.z, xa.w}, df{xb.z, xb.w}), ckx));
         yre.add(df_mul_raw(df_pair(df{ya.x, ya.y}, df{yb.x, yb.y}), cky));
         yim.add(df_mul_raw(df_pair(df{ya.z, ya.w}, df{yb.z, yb.w}), cky));
-        zre.add(df_mul_raw(df_pair(za.re, zb.re), ckz));
-        zim.add(df_mul_raw(df_pair(za.im, zb.im), ckz));
+        zre.add(df_mul_raw(df_pair(df{za.x, za.y}, df{zb.x, zb.y}), ckz));
+        zim.add(df_mul_raw(df_pair(df{za.z, za.w}, df{zb.z, zb.w}), ckz));
       }
       dre.add(acc_df(xre));
       dre.add(acc_df(yre));

@@ -874,7 +874,12 @@ __global__ void k_cplx_to_df(const double2* x, float4* y, long long n) {
 
 template <int R>
 cudaError_t stencil_df_r(dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a, bool prepare) {
-  if (prepare) return cudaFuncSetAttribute(k_stencil_df<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (prepare) {
+    // all of the SM's unified memory as shared memory, so that two blocks fit
+    cudaError_t e = cudaFuncSetAttribute(k_stencil_df<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_stencil_df<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   k_stencil_df<R><<<grid, threads, smem, s>>>(a);
   return cudaSuccess;
 }
@@ -955,8 +960,10 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   const long long n = g.n, nxy = g.nxy;
   const int nlp = (int)ctx->lplanes.size(), nrp = (int)ctx->rplanes.size();
   const long long no = (long long)std::max(nlp, nrp) * nxy;
-  const TileShape ts = choose_tiles(g, 2, sizeof(double2), StencilMax<double>::threads, ctx->opts.tile_y,
-                                    ctx->opts.slab);
+  // the double-float stencil spends a larger share on the 2R-plane prologue of a slab,
+  // so its default slab is deeper
+  const int slab = ctx->opts.slab > 0 ? ctx->opts.slab : (dfm ? 64 : 0);
+  const TileShape ts = choose_tiles(g, 2, sizeof(double2), StencilMax<double>::threads, ctx->opts.tile_y, slab);
   const int nblk_st = ts.ntx * ts.nty * ts.nslab;
   const int nblk3 = (int)std::min(1024LL, (n + 256 * 8 - 1) / (256 * 8));
   const long long np = no;
@@ -1042,7 +1049,8 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   a.tol = ctx->opts.tol; a.maxit = ctx->opts.maxit; a.escale = B.escale;
   a.res_t = res_t; a.res_it = res_it; a.res_st = res_st;
 
-  if (dfm) MS_CK(stencil_df(g.R, dim3(1), 0, ts.smem, st, StencilDfArgs{}, true));
+  const size_t smem_df = stencil_df_smem(g.R, ts.TX, ts.TY, 2, ts.threads);
+  if (dfm) MS_CK(stencil_df(g.R, dim3(1), 0, smem_df, st, StencilDfArgs{}, true));
   else MS_CK(prepare_stencil<double>(g.R, ts.smem));
   StencilDfArgs da{};
   da.r = reinterpret_cast<const float4*>(B.R); da.q = reinterpret_cast<float4*>(B.Q); da.part = B.sig_part;
@@ -1126,7 +1134,7 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
     da.p_in = reinterpret_cast<const float4*>(sa.p_in);
     da.p_out = reinterpret_cast<float4*>(sa.p_out);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 0], st, cudaEventRecordExternal);
-    if (dfm) stencil_df(g.R, sgrid, ts.threads, ts.smem, st, da, false);
+    if (dfm) stencil_df(g.R, sgrid, ts.threads, smem_df, st, da, false);
     else launch_stencil<double>(g.R, sgrid, ts.threads, ts.smem, st, sa);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 1], st, cudaEventRecordExternal);
     k_ms_coef<<<S, 256, 0, st>>>(a);
