@@ -477,6 +477,8 @@ def run_sketch(args):
         got = results[0]
         okp = (ref["status"][0] == 0) & (got["status"][0] == 0)
         parity = {"window_energies": W, "k_index": k,
+                  "seed_iterations_mean_fp64": float(ref["iters"][0].mean()),
+                  "seed_iterations_mean_df64": float(got["iters"][0].mean()),
                   "max_abs_dT_vs_fp64": float(np.abs(got["T"][0][okp] - ref["T"][0][okp]).max()),
                   "max_abs_dT_minus_vs_fp64": float(np.abs(got["T_minus"][0][okp] - ref["T_minus"][0][okp]).max()),
                   "fp64_all_converged": bool(np.all(ref["status"] == 0))}

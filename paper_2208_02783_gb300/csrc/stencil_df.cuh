@@ -37,7 +37,9 @@ struct StencilDfArgs {
   long long slot_stride;
 };
 
-constexpr int kDfThreads = 448;
+// Up to 896 threads per block (73 registers each): a 20 x 20 plane with both halves
+// fits one block, so both lateral halos come from the block's own points.
+constexpr int kDfThreads = 896;
 
 // 2^k as a float (|k| <= 126), exact
 __device__ inline float pow2f(int k) {
@@ -62,7 +64,7 @@ __host__ __device__ inline size_t stencil_df_smem(int R, int TX, int TY, int H, 
 }
 
 template <int R>
-__global__ void __launch_bounds__(kDfThreads, 2) k_stencil_df(const StencilDfArgs a) {
+__global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2][32];
   float4* sm = reinterpret_cast<float4*>(smem_raw);
@@ -128,12 +130,16 @@ __global__ void __launch_bounds__(kDfThreads, 2) k_stencil_df(const StencilDfArg
     np = pin[(long long)(z0 + R) * nxy + pidx];
   }
   // a tile as wide as the cell (one wrap at most) takes its x-halo from its own
-  // points: the cell at x + nx is exp(i k L_a) p(x), the cell at x - nx is exp(-i k L_a) p(x)
+  // points: the cell at x + nx is exp(i k L_a) p(x), the cell at x - nx is exp(-i k L_a) p(x);
+  // likewise in y for a tile as high as the cell
   const bool xself = TX == nx && nx >= R;
+  const bool yself = TY == ny && ny >= R;
 
   dfacc sg_re, sg_im;
-  const int nh = 2 * R * (TX + TY);
-  const int h0 = xself ? 2 * R * TY : 0;  // first halo cell computed from global memory
+  // halo cells still computed from global memory: the x-halo rows come first in the
+  // enumeration below, then the y-halo columns
+  const int nh = yself ? 2 * R * TY : 2 * R * (TX + TY);
+  const int h0 = xself ? 2 * R * TY : 0;
   for (int zc = z0; zc < z1; ++zc) {
     {
       const int z = zc + R;
@@ -152,6 +158,10 @@ __global__ void __launch_bounds__(kDfThreads, 2) k_stencil_df(const StencilDfArg
     if (xself && inside) {
       if (tx < R) my[(ty + R) * SW + tx + R + nx] = dfc_store(dfc_mul(c, dfc_load(ph[kPhaseW + 1])));
       if (tx >= nx - R) my[(ty + R) * SW + tx + R - nx] = dfc_store(dfc_mul(c, dfc_load(ph[kPhaseW - 1])));
+    }
+    if (yself && inside) {
+      if (ty < R) my[(ty + R + ny) * SW + tx + R] = dfc_store(dfc_mul(c, dfc_load(ph[kPhaseN + kPhaseW + 1])));
+      if (ty >= ny - R) my[(ty + R - ny) * SW + tx + R] = dfc_store(dfc_mul(c, dfc_load(ph[kPhaseN + kPhaseW - 1])));
     }
     for (int h = worker ? h0 + lt : nh; h < nh; h += npt) {
       int hx, hy;

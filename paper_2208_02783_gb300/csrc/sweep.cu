@@ -963,7 +963,8 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   // the double-float stencil spends a larger share on the 2R-plane prologue of a slab,
   // so its default slab is deeper
   const int slab = ctx->opts.slab > 0 ? ctx->opts.slab : (dfm ? 64 : 0);
-  const TileShape ts = choose_tiles(g, 2, sizeof(double2), StencilMax<double>::threads, ctx->opts.tile_y, slab);
+  const TileShape ts = choose_tiles(g, 2, sizeof(double2), dfm ? kDfThreads : StencilMax<double>::threads,
+                                    ctx->opts.tile_y, slab);
   const int nblk_st = ts.ntx * ts.nty * ts.nslab;
   const int nblk3 = (int)std::min(1024LL, (n + 256 * 8 - 1) / (256 * 8));
   const long long np = no;

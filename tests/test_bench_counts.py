@@ -44,3 +44,30 @@ def test_k_pair_representatives_cover_the_mesh_once():
         assert j not in reps  # the mirror -k is not itself a representative
         seen.update({i, j})
     assert seen == set(range(len(kk)))
+
+
+def test_double_float_stencil_op_count():
+    # FP32 operations of the double-float primitives: TwoSum 6, FastTwoSum 3, product
+    # with FMA (1 multiply + 3 FMA) 4, lazy accumulation (TwoSum + 2 adds) 8, accurate
+    # double-word sum (2 TwoSum + 2 FastTwoSum + 2 adds) 20
+    two_sum, fast, prod, acc, dadd = 6, 3, 4, 8, 20
+    cmul = 4 * prod + 2 * (two_sum + 2 + fast)  # complex double-float product
+    p_update = cmul + 2 * dadd
+    diagonal = dadd + 4 * prod + 4 * acc
+    pair = two_sum + 2
+    combine = 6 * acc + 2 * fast
+    dot = 8 + 4 * prod + 4 * acc
+    for order in (2, 4, 8, 12):
+        r = order // 2
+        want = p_update + diagonal + r * 6 * (pair + prod + acc) + combine + dot
+        assert bench.stencil_df_ops_per_point(order) == want
+
+
+def test_sketch_plan_is_seeded_and_in_range():
+    kk, _ = monkhorst_pack(8, 8)
+    reps = bench.k_representatives(kk)
+    a = bench.sketch_plan(256, reps, 40, 16)
+    b = bench.sketch_plan(256, reps, 40, 16)
+    assert a == b
+    assert all(k in reps and 0 <= e <= 256 - 16 for k, e in a)
+    assert len({k for k, _ in a}) > 5 and len({e for _, e in a}) > 10
