@@ -62,3 +62,38 @@ def test_gradients_match_finite_differences(name):
         flat[i] = old
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g[name].reshape(-1)[i]) <= 1e-6 * max(1e-3, abs(fd)), (name, i, fd)
+
+
+def test_bf16_round_is_nearest_even_with_8_significant_bits():
+    # exact cases: ties go to the even 7-bit fraction
+    cases = {1.0: 1.0, 1.0 + 2**-8: 1.0, 1.0 + 3 * 2**-8: 1.0 + 2**-6, 1.0 + 2**-7: 1.0 + 2**-7,
+             -(1.0 + 2**-8 + 2**-12): -(1.0 + 2**-7), 3.0: 3.0, 0.0: 0.0, 2.0**-100: 2.0**-100}
+    for x, want in cases.items():
+        assert unet.bf16_round(np.array([x]))[0] == want, x
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=10000) * 10.0 ** rng.uniform(-20, 20, 10000)
+    r = unet.bf16_round(a)
+    assert np.all(np.abs(r - a) <= 2.0**-8 * np.abs(a))  # half an ulp of an 8-bit significand
+    assert np.array_equal(unet.bf16_round(r), r)  # idempotent
+    # the rounded values have at most 8 significant bits
+    m, _ = np.frexp(r[r != 0])
+    assert np.all(m * 2**8 == np.round(m * 2**8))
+
+
+def test_adam_step_closed_forms():
+    # a constant gradient g: the bias-corrected moments are g and g^2 at every step, so
+    # each step moves by lr g / (|g| + eps)
+    g = np.array([0.3, -2.0, 1e-3, 0.0])
+    p = np.array([1.0, 1.0, 1.0, 1.0])
+    m = np.zeros(4)
+    v = np.zeros(4)
+    lr, eps = 1e-2, 1e-8
+    for t in range(1, 5):
+        p_new, m, v = unet.adam_step(p, g, m, v, t, lr, eps=eps)
+        assert np.allclose(p_new - p, -lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+        p = p_new
+    # first step from zero moments with different b1, b2: the same closed form
+    p1, m1, v1 = unet.adam_step(np.zeros(2), np.array([2.0, -0.5]), np.zeros(2), np.zeros(2), 1, 0.1,
+                                b1=0.5, b2=0.25)
+    assert np.allclose(p1, -0.1 * np.array([2.0, -0.5]) / (np.array([2.0, 0.5]) + 1e-8))
+    assert np.allclose(m1, [1.0, -0.25]) and np.allclose(v1, [3.0, 0.1875])
