@@ -68,14 +68,17 @@ def stencil_flops_per_point(order: int) -> int:
     return 18 * (order // 2) + 22
 
 
-def stencil_df_ops_per_point(order: int) -> int:
+def stencil_df_ops_per_point(order: int, iso: bool = False) -> int:
     """FP32 operations of the double-float stencil per grid point and half, counted
     from its algorithm (halo recomputation excluded): p = r + beta p (complex
     double-float multiply 38 + accurate add 2 x 20 = 78), diagonal term (accurate
-    subtraction 20, four products 16, four accumulations 32 = 68), per neighbour pair
-    and axis and component 20 (TwoSum pair 8, product 4, accumulation 8) = 120 R,
-    combining the axes 54, pairing dot with its scaling 56."""
-    return 78 + 68 + 120 * (order // 2) + 54 + 56
+    subtraction 20, four products 16, four accumulations 32 = 68), per distance m and
+    component either 3 x (TwoSum pair 8, product 4, accumulation 8) = 60, or, with the
+    same spacing on the three axes (iso), three pairs 24, their two sums 16, one
+    product 4 and one accumulation 8 = 52; combining the axes 54, pairing dot with its
+    scaling 56."""
+    per_m = 2 * (52 if iso else 60)
+    return 78 + 68 + per_m * (order // 2) + 54 + 56
 
 
 def stencil_bytes_per_point(elem: int) -> int:
@@ -500,7 +503,8 @@ def run_sketch(args):
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     if prec == pkg.PREC_DF64:
-        ops = stencil_df_ops_per_point(g.order) * ph_per_launch
+        iso = g.hx == g.hy == g.hz
+        ops = stencil_df_ops_per_point(g.order, iso) * ph_per_launch
         achieved = ops / (st_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_OPS_PEAK_T, "unit": "T FP32-op/s",
                 "frac": achieved / FP32_OPS_PEAK_T,

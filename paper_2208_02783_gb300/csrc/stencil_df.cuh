@@ -63,7 +63,9 @@ __host__ __device__ inline size_t stencil_df_smem(int R, int TX, int TY, int H, 
   return (size_t)H * (TX + 2 * R) * (TY + 2 * R) * sizeof(float4) + (size_t)(2 * R + 1) * threads * sizeof(float4);
 }
 
-template <int R>
+// ISO: the three axes share the coefficients (hx = hy = hz), so the six neighbours at
+// distance m are summed first and multiplied once.
+template <int R, bool ISO>
 __global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[2][32];
@@ -196,12 +198,20 @@ __global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArg
         const float4 za = ring[rpos(zc + m) * rs], zb = ring[rpos(zc - m + 2 * R + 1) * rs];
         const df ckx = df{a.kx[m].x, a.kx[m].y}, cky = df{a.ky[m].x, a.ky[m].y},
                  ckz = df{a.kz[m].x, a.kz[m].y};
-        xre.add(df_mul_raw(df_pair(df{xa.x, xa.y}, df{xb.x, xb.y}), ckx));
-        xim.add(df_mul_raw(df_pair(df{xa.z, xa.w}, df{xb.z, xb.w}), ckx));
-        yre.add(df_mul_raw(df_pair(df{ya.x, ya.y}, df{yb.x, yb.y}), cky));
-        yim.add(df_mul_raw(df_pair(df{ya.z, ya.w}, df{yb.z, yb.w}), cky));
-        zre.add(df_mul_raw(df_pair(df{za.x, za.y}, df{zb.x, zb.y}), ckz));
-        zim.add(df_mul_raw(df_pair(df{za.z, za.w}, df{zb.z, zb.w}), ckz));
+        const df sxr = df_pair(df{xa.x, xa.y}, df{xb.x, xb.y}), sxi = df_pair(df{xa.z, xa.w}, df{xb.z, xb.w});
+        const df syr = df_pair(df{ya.x, ya.y}, df{yb.x, yb.y}), syi = df_pair(df{ya.z, ya.w}, df{yb.z, yb.w});
+        const df szr = df_pair(df{za.x, za.y}, df{zb.x, zb.y}), szi = df_pair(df{za.z, za.w}, df{zb.z, zb.w});
+        if (ISO) {
+          xre.add(df_mul_raw(df_pair(df_pair(sxr, syr), szr), ckx));
+          xim.add(df_mul_raw(df_pair(df_pair(sxi, syi), szi), ckx));
+        } else {
+          xre.add(df_mul_raw(sxr, ckx));
+          xim.add(df_mul_raw(sxi, ckx));
+          yre.add(df_mul_raw(syr, cky));
+          yim.add(df_mul_raw(syi, cky));
+          zre.add(df_mul_raw(szr, ckz));
+          zim.add(df_mul_raw(szi, ckz));
+        }
       }
       dre.add(acc_df(xre));
       dre.add(acc_df(yre));

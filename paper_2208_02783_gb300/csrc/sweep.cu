@@ -872,30 +872,38 @@ __global__ void k_cplx_to_df(const double2* x, float4* y, long long n) {
     y[i] = dfc_from_double2(x[i]);
 }
 
-template <int R>
+template <int R, bool ISO>
 cudaError_t stencil_df_r(dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a, bool prepare) {
   if (prepare) {
-    // all of the SM's unified memory as shared memory, so that two blocks fit
-    cudaError_t e = cudaFuncSetAttribute(k_stencil_df<R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    // all of the SM's unified memory as shared memory (the z-ring is large)
+    cudaError_t e = cudaFuncSetAttribute(k_stencil_df<R, ISO>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_stencil_df<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_stencil_df<R, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
-  k_stencil_df<R><<<grid, threads, smem, s>>>(a);
+  k_stencil_df<R, ISO><<<grid, threads, smem, s>>>(a);
   return cudaSuccess;
 }
 
-// prepare = true sets the kernel's shared-memory limit; false launches it
-cudaError_t stencil_df(int R, dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a,
-                       bool prepare) {
+template <bool ISO>
+cudaError_t stencil_df_iso(int R, dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a,
+                           bool prepare) {
   switch (R) {
-    case 1: return stencil_df_r<1>(grid, threads, smem, s, a, prepare);
-    case 2: return stencil_df_r<2>(grid, threads, smem, s, a, prepare);
-    case 3: return stencil_df_r<3>(grid, threads, smem, s, a, prepare);
-    case 4: return stencil_df_r<4>(grid, threads, smem, s, a, prepare);
-    case 5: return stencil_df_r<5>(grid, threads, smem, s, a, prepare);
-    case 6: return stencil_df_r<6>(grid, threads, smem, s, a, prepare);
+    case 1: return stencil_df_r<1, ISO>(grid, threads, smem, s, a, prepare);
+    case 2: return stencil_df_r<2, ISO>(grid, threads, smem, s, a, prepare);
+    case 3: return stencil_df_r<3, ISO>(grid, threads, smem, s, a, prepare);
+    case 4: return stencil_df_r<4, ISO>(grid, threads, smem, s, a, prepare);
+    case 5: return stencil_df_r<5, ISO>(grid, threads, smem, s, a, prepare);
+    case 6: return stencil_df_r<6, ISO>(grid, threads, smem, s, a, prepare);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// prepare = true sets the kernel's shared-memory limit; false launches it.  iso: the
+// three axes have the same spacing (one coefficient per distance)
+cudaError_t stencil_df(int R, bool iso, dim3 grid, int threads, size_t smem, cudaStream_t s,
+                       const StencilDfArgs& a, bool prepare) {
+  return iso ? stencil_df_iso<true>(R, grid, threads, smem, s, a, prepare)
+             : stencil_df_iso<false>(R, grid, threads, smem, s, a, prepare);
 }
 
 // ---------------------------------------------------------------------------------
@@ -966,7 +974,11 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   const TileShape ts = choose_tiles(g, 2, sizeof(double2), dfm ? kDfThreads : StencilMax<double>::threads,
                                     ctx->opts.tile_y, slab);
   const int nblk_st = ts.ntx * ts.nty * ts.nslab;
-  const int nblk3 = (int)std::min(1024LL, (n + 256 * 8 - 1) / (256 * 8));
+  // blocks per run of the vector update: the double-float update sets up its scalars
+  // in FP64 once per thread, so it takes more points per thread (about 8 blocks per SM
+  // over all runs)
+  const int nblk3 = dfm ? (int)std::max(4LL, std::min((n + 256 * 8 - 1) / (256 * 8), (152LL * 8 + S - 1) / S))
+                        : (int)std::min(1024LL, (n + 256 * 8 - 1) / (256 * 8));
   const long long np = no;
   const size_t need_vec = (size_t)S * 2 * n, need_shv = (size_t)S * ne * 2 * no;
   const size_t need_rnd = (size_t)std::max(1, nrep) * 2 * std::max(1, smax) * np;
@@ -1051,7 +1063,9 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   a.res_t = res_t; a.res_it = res_it; a.res_st = res_st;
 
   const size_t smem_df = stencil_df_smem(g.R, ts.TX, ts.TY, 2, ts.threads);
-  if (dfm) MS_CK(stencil_df(g.R, dim3(1), 0, smem_df, st, StencilDfArgs{}, true));
+  bool iso = true;
+  for (int m = 1; m <= g.R; ++m) iso = iso && g.kx[m] == g.ky[m] && g.kx[m] == g.kz[m];
+  if (dfm) MS_CK(stencil_df(g.R, iso, dim3(1), 0, smem_df, st, StencilDfArgs{}, true));
   else MS_CK(prepare_stencil<double>(g.R, ts.smem));
   StencilDfArgs da{};
   da.r = reinterpret_cast<const float4*>(B.R); da.q = reinterpret_cast<float4*>(B.Q); da.part = B.sig_part;
@@ -1135,7 +1149,7 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
     da.p_in = reinterpret_cast<const float4*>(sa.p_in);
     da.p_out = reinterpret_cast<float4*>(sa.p_out);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 0], st, cudaEventRecordExternal);
-    if (dfm) stencil_df(g.R, sgrid, ts.threads, smem_df, st, da, false);
+    if (dfm) stencil_df(g.R, iso, sgrid, ts.threads, smem_df, st, da, false);
     else launch_stencil<double>(g.R, sgrid, ts.threads, ts.smem, st, sa);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 1], st, cudaEventRecordExternal);
     k_ms_coef<<<S, 256, 0, st>>>(a);

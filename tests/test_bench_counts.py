@@ -61,6 +61,10 @@ def test_double_float_stencil_op_count():
         r = order // 2
         want = p_update + diagonal + r * 6 * (pair + prod + acc) + combine + dot
         assert bench.stencil_df_ops_per_point(order) == want
+        # equal spacings: per distance and component three pairs, two sums of them, one
+        # product and one accumulation
+        want_iso = p_update + diagonal + r * 2 * (3 * pair + 2 * pair + prod + acc) + combine + dot
+        assert bench.stencil_df_ops_per_point(order, iso=True) == want_iso
 
 
 def test_sketch_plan_is_seeded_and_in_range():

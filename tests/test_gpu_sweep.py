@@ -134,3 +134,20 @@ def test_sweep_argument_checks():
             tr.shifted_columns([0.3], [0], [10 ** 6])
         with pytest.raises(pkg.TransecError):
             tr.shifted_columns([float("nan")], [0], [1])
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_sketch_unequal_spacings(precision):
+    """hx, hy, hz all different: the stencil takes each axis's own coefficients."""
+    need_gpu()
+    kf = (0.3125, -0.4375)
+    inst = small_instance(6, 5, 40, 0.45, 8, 8, v_amp=0.7, kfrac=(kf,), energies=(0.3,), seed=23,
+                          hy=0.5, hz=0.4)
+    g = inst.grid
+    energies = np.array([0.2, 0.45, 0.7])
+    with context(inst, precision=precision) as tr:
+        r = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=4)
+    assert np.all(r["status"] == 0)
+    for s, e in enumerate(energies):
+        tp, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf)
+        assert abs(r["T"][0, s] - tp) <= TOL_T
