@@ -551,6 +551,7 @@ def run_sketch(args):
                                 "estimated from independent halves of the runs)",
             "mean_seed_iterations": float(its.mean()), "max_seed_iterations": int(its.max()),
             "failed_results": int((~ok).sum()), "max_abs_T_k_minus_T_mk": pm_diff,
+            "results_redone_in_fp64": int(sw.get("fp64_redone", 0)),
             "min_rank": int(np.concatenate([r["rank"][0] for r in results]).min()),
             "parity_vs_fp64": parity,
             "l2": "per-step working set (36 runs x 2 halves x 192,000 points x 4 vectors x 16 B = 0.9 GB, plus "

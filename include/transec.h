@@ -102,6 +102,11 @@ typedef struct transec_solver_opts {
                          device-side WHILE loop runs chunk after chunk until the queue is
                          drained (bounded by maxit); != 0: the host launches and polls one
                          chunk graph at a time (always the case when profile != 0) */
+  int df_stall_its;   /* double-float multi-shift runs: once a run has gone this many
+                         iterations without a new shift converging (counted from its
+                         first convergence, or 3x this from the start), its remaining
+                         shifts stop and are solved again in FP64; default 8000,
+                         negative = never */
 } transec_solver_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -362,9 +367,11 @@ int transec_shifted_column(transec_ctx* ctx, int ne, const double* energies, int
  * status_out[i*ne + s] (may be NULL).  Runs retire and refill on the GPU as in the
  * plain engine (opts.slots runs in flight, 0 = chosen from the grid size and free
  * memory); the whole solve is one graph launch with a device-side loop unless
- * opts.profile or opts.host_loop is set.  Host arrays; 1 <= ne <= 1024.  Failed
- * (E, item) results get t = NaN and the call returns the most severe status.
- * Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT.
+ * opts.profile or opts.host_loop is set.  With opts.precision = TRANSEC_PREC_DF64 the
+ * runs are double-float, and the (item, energy) results that do not converge that way
+ * (or stop under opts.df_stall_its) are solved again in FP64 within the call.  Host
+ * arrays; 1 <= ne <= 1024.  Failed (E, item) results get t = NaN and the call returns
+ * the most severe status.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT.
  */
 int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, int nitems,
                             const int* ik, const int64_t* cols, double* t_out, double* t_minus_out,
@@ -389,7 +396,10 @@ int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, in
  * estimate, so |T - T_minus| gauges the sketch error); rank_out = directions of Y kept;
  * status_out per result; iters_out = seed iterations at which the energy converged in
  * its slowest run.  1 <= s_left <= 32, s_left <= s_right <= 64, 1 <= ne <= 1024.  All
- * nrep * (s_left + s_right) runs are in flight at once (no refill).  Host arrays.
+ * nrep * (s_left + s_right) runs are in flight at once (no refill).  With
+ * opts.precision = TRANSEC_PREC_DF64 the runs are double-float, and the (k, energy)
+ * results that do not converge that way (or stop under opts.df_stall_its) are
+ * computed again with FP64 runs within the call.  Host arrays.
  * Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT; per-result ENOCONV / EBREAKDOWN with
  * T = NaN.
  */
@@ -401,13 +411,14 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
 /*
  * Counters of the multi-shift engine since the last transec_stats_reset: seed
  * iterations summed over runs, per-shift point updates (kept points x halves x
- * iterations of each shift), and with opts.profile set the event-timed stencil and
- * shifted-update kernels (ms, launches) and the sketch reduction (ms).  Any output
- * may be NULL.
+ * iterations of each shift), with opts.profile set the event-timed stencil and
+ * shifted-update kernels (ms, launches) and the sketch reduction (ms), and the
+ * (energy, column or k) results of double-float calls that were solved again in FP64
+ * (fp64_redone).  Any output may be NULL.
  */
 int transec_sweep_stats(const transec_ctx* ctx, long long* iters, long long* shift_points,
                         double* stencil_ms, long long* stencil_launches, double* shift_ms,
-                        long long* shift_launches, double* reduce_ms);
+                        long long* shift_launches, double* reduce_ms, long long* fp64_redone);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next
  * call on the same context. */

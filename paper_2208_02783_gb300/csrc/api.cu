@@ -95,6 +95,7 @@ void default_opts(transec_solver_opts* o) {
   if (o->reliable <= 0 || o->reliable >= 1) o->reliable = 1e-5;
   if (o->mixed_maxit <= 0) o->mixed_maxit = 8000;
   if (o->mixed_decade_its == 0) o->mixed_decade_its = 1000;
+  if (o->df_stall_its == 0) o->df_stall_its = 8000;
 }
 
 // Bloch phase exp(2 pi i kappa w) with the argument reduced before the cosine.
@@ -1436,13 +1437,15 @@ int transec_stats_reset(transec_ctx* ctx) {
   ctx->sweep_iters = ctx->sweep_shift_points = 0;
   ctx->sweep_stencil_ms = ctx->sweep_shift_ms = ctx->sweep_update_ms = ctx->sweep_reduce_ms = 0;
   ctx->sweep_stencil_launches = ctx->sweep_shift_launches = 0;
+  ctx->sweep_fp64_redone = 0;
   return TRANSEC_OK;
 }
 
 int transec_sweep_stats(const transec_ctx* ctx, long long* iters, long long* shift_points,
                         double* stencil_ms, long long* stencil_launches, double* shift_ms,
-                        long long* shift_launches, double* reduce_ms) {
+                        long long* shift_launches, double* reduce_ms, long long* fp64_redone) {
   if (!ctx) return TRANSEC_EINVAL;
+  if (fp64_redone) *fp64_redone = ctx->sweep_fp64_redone;
   if (iters) *iters = ctx->sweep_iters;
   if (shift_points) *shift_points = ctx->sweep_shift_points;
   if (stencil_ms) *stencil_ms = ctx->sweep_stencil_ms;

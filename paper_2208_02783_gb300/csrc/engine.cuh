@@ -115,4 +115,5 @@ struct transec_ctx {
   long long sweep_iters = 0, sweep_shift_points = 0;
   double sweep_stencil_ms = 0, sweep_shift_ms = 0, sweep_update_ms = 0, sweep_reduce_ms = 0;
   long long sweep_stencil_launches = 0, sweep_shift_launches = 0;
+  long long sweep_fp64_redone = 0;  // double-float results solved again in FP64
 };

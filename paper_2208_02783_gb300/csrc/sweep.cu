@@ -214,6 +214,7 @@ struct MsArgs {
   int nblk_st;
   double tol;
   int maxit;
+  int stall_its;           // > 0: a run stops once no shift has converged for this long
   int* escale;             // [S]
   // UNIT results: [item][shift][2] t, [item][shift] iterations and status
   double* res_t;
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(256) k_ms_scalars(const MsArgs a) {
   const double thresh = a.tol * a.ms[slot].bnorm;
   const bool brk = !(isfinite(rho_new.x) && isfinite(rho_new.y)) ||
                    (rho_new.x == 0.0 && rho_new.y == 0.0) || !isfinite(rn);
-  int live = 0;
+  int live = 0, fresh = 0;
   for (int s = threadIdx.x; s < a.ne; s += blockDim.x) {
     MsShift& z = a.sh[(long long)slot * a.ne + s];
     if (!z.active) continue;
@@ -486,6 +487,7 @@ __global__ void __launch_bounds__(256) k_ms_scalars(const MsArgs a) {
       z.active = 0;
       z.status = kOK;
       z.conv_it = it;
+      ++fresh;
     } else if (brk || !isfinite(res)) {
       z.active = 0;
       z.status = kEBREAKDOWN;
@@ -498,12 +500,34 @@ __global__ void __launch_bounds__(256) k_ms_scalars(const MsArgs a) {
       ++live;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) live += __shfl_down_sync(0xffffffffu, live, o);
-  if ((threadIdx.x & 31) == 0) s_live[threadIdx.x >> 5] = live;
+  const int packed = live + (fresh << 16);  // at most 1024 shifts each
+  int sum = packed;
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) s_live[threadIdx.x >> 5] = sum;
   __syncthreads();
+  // stall rule (double-float runs): no new convergence for stall_its iterations since
+  // the last one (3 stall_its before the first) stops the remaining shifts
+  __shared__ int s_stop;
   if (threadIdx.x == 0) {
     int tot = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_live[w];
+    const int nlive = tot & 0xffff, nfresh = tot >> 16;
+    if (nfresh > 0) st.it_best = it;  // iteration of the latest shift convergence
+    s_stop = nlive > 0 && a.stall_its > 0 &&
+             (st.it_best > 0 ? it - st.it_best > a.stall_its : it > 3 * a.stall_its);
+    s_live[0] = s_stop ? 0 : nlive;
+  }
+  __syncthreads();
+  if (s_stop)
+    for (int s = threadIdx.x; s < a.ne; s += blockDim.x) {
+      MsShift& z = a.sh[(long long)slot * a.ne + s];
+      if (!z.active) continue;
+      z.active = 0;
+      z.status = kENOCONV;
+      z.conv_it = it;
+    }
+  if (threadIdx.x == 0) {
+    const int tot = s_live[0];
     st.it = it;
     st.res = rn;
     if (tot == 0) {
@@ -1060,6 +1084,7 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   a.lrank = B.lrank; a.rrank = B.rrank; a.nlp = nlp; a.nrp = nrp; a.gl = ctx->d_gl; a.gr = ctx->d_gr;
   a.rho_part = B.rho_part; a.nblk3 = nblk3; a.sig_part = B.sig_part; a.nblk_st = nblk_st;
   a.tol = ctx->opts.tol; a.maxit = ctx->opts.maxit; a.escale = B.escale;
+  a.stall_its = dfm ? ctx->opts.df_stall_its : 0;
   a.res_t = res_t; a.res_it = res_it; a.res_st = res_st;
 
   const size_t smem_df = stencil_df_smem(g.R, ts.TX, ts.TY, 2, ts.threads);
@@ -1265,93 +1290,74 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, int nitems, const int* ik,
-                            const int64_t* cols, double* t_out, double* t_minus_out, int* iters_out,
-                            int* status_out) {
-  if (!ctx) return TRANSEC_EINVAL;
-  if (!ctx->have_v || !ctx->have_abc || !ctx->have_k)
-    return ms_fail(ctx, TRANSEC_ESTATE, "potential, absorbing boundary and k-mesh must be set");
-  if (ne < 1 || ne > 1024 || nitems < 0 || !energies || (nitems > 0 && (!ik || !cols || !t_out)))
-    return ms_fail(ctx, TRANSEC_EINVAL, "bad multi-shift arguments (1 <= ne <= 1024)");
-  if (nitems == 0) return TRANSEC_OK;
-  const long long nrhs = (long long)ctx->lplanes.size() * ctx->g.nxy;
-  for (int e = 0; e < ne; ++e)
-    if (!std::isfinite(energies[e])) return ms_fail(ctx, TRANSEC_EINVAL, "non-finite energy");
-  std::vector<MsItem> items(nitems);
-  for (int i = 0; i < nitems; ++i) {
-    if (ik[i] < 0 || ik[i] >= ctx->nk) return ms_fail(ctx, TRANSEC_EINVAL, "k index out of range");
-    if (cols[i] < 0 || cols[i] >= nrhs) return ms_fail(ctx, TRANSEC_EINVAL, "column out of range");
-    items[i] = MsItem{ik[i], RUN_UNIT, 0, 0, (long long)cols[i]};
-  }
-  if (ctx->rplanes.empty()) return ms_fail(ctx, TRANSEC_EINVAL, "right absorbing profile is zero everywhere");
-  DevScope ds(ctx->device);
-  MS_CK(cudaStreamSynchronize(ctx->user));
-  std::vector<double> es(energies, energies + ne), sorted = es;
-  std::sort(sorted.begin(), sorted.end());
-  const double e0 = sorted[ne / 2];
-  // runs in flight: enough point-halves to fill the GPU, bounded by memory
+// Results of one multi-shift call, row-major [item or k group][energy].
+struct SweepOut {
+  std::vector<double> t, tm;
+  std::vector<int> it, st, rank;
+};
+
+// Runs in flight for UNIT items: enough point-halves to fill the GPU, bounded by memory.
+long long unit_slots(transec_ctx* ctx, int ne, int nitems) {
   const long long n = ctx->g.n;
   const long long no = (long long)std::max(ctx->lplanes.size(), ctx->rplanes.size()) * ctx->g.nxy;
   const size_t per_slot = (size_t)4 * 2 * n * 16 + (size_t)2 * ne * 2 * no * 16;
   long long S = ctx->opts.slots > 0 ? ctx->opts.slots : std::max(1LL, (24LL << 20) / (2 * n));
   size_t fr = 0, tot = 0;
   if (cudaMemGetInfo(&fr, &tot) == cudaSuccess) S = std::min<long long>(S, std::max<long long>(1, fr / 2 / per_slot));
-  S = std::max(1LL, std::min<long long>(S, nitems));
+  return std::max(1LL, std::min<long long>(S, nitems));
+}
+
+double seed_energy(const std::vector<double>& es) {
+  std::vector<double> sorted = es;
+  std::sort(sorted.begin(), sorted.end());
+  return sorted[sorted.size() / 2];
+}
+
+// Unit columns (k index, left-CAP column) at the energies es, in the context's
+// precision.  Outputs [item][energy].
+int columns_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vector<int>& ik,
+                  const std::vector<long long>& cols, SweepOut& out) {
+  const int ne = (int)es.size(), nitems = (int)ik.size();
+  std::vector<MsItem> items(nitems);
+  for (int i = 0; i < nitems; ++i) items[i] = MsItem{ik[i], RUN_UNIT, 0, 0, cols[i]};
   if (!ctx->sweep) ctx->sweep = new SweepBufs();
   double* rt = nullptr;
   int *rit = nullptr, *rst = nullptr;
-  int rc = run_sweep(ctx, items, es, e0, (int)S, 0, 0, 0ULL, &rt, &rit, &rst);
-  int worst = TRANSEC_OK;
+  const int S = (int)unit_slots(ctx, ne, nitems);
+  int rc = run_sweep(ctx, items, es, seed_energy(es), S, 0, 0, 0ULL, &rt, &rit, &rst);
   if (rc == TRANSEC_OK) {
-    std::vector<double> t((size_t)nitems * ne * 2);
-    std::vector<int> it((size_t)nitems * ne), sst((size_t)nitems * ne);
+    const size_t m = (size_t)nitems * ne;
+    std::vector<double> t(2 * m);
+    out.it.assign(m, 0);
+    out.st.assign(m, 0);
     cudaError_t e = cudaMemcpy(t.data(), rt, t.size() * sizeof(double), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(it.data(), rit, it.size() * sizeof(int), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(sst.data(), rst, sst.size() * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out.it.data(), rit, m * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(out.st.data(), rst, m * sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
       cudaGetLastError();
       rc = ms_fail(ctx, TRANSEC_ECUDA, std::string("multi-shift results: ") + cudaGetErrorString(e));
     } else {
-      for (size_t u = 0; u < (size_t)nitems * ne; ++u) {
-        t_out[u] = t[2 * u];
-        if (t_minus_out) t_minus_out[u] = t[2 * u + 1];
-        if (iters_out) iters_out[u] = it[u];
-        if (status_out) status_out[u] = sst[u];
-        if (ms_severity(sst[u]) > ms_severity(worst)) worst = sst[u];
+      out.t.resize(m);
+      out.tm.resize(m);
+      for (size_t u = 0; u < m; ++u) {
+        out.t[u] = t[2 * u];
+        out.tm[u] = t[2 * u + 1];
       }
     }
   }
   cudaFree(rt);
   cudaFree(rit);
   cudaFree(rst);
-  if (rc != TRANSEC_OK) return rc;
-  if (worst != TRANSEC_OK) ctx->err = std::string("some columns failed: ") + transec_status_string(worst);
-  return worst;
+  return rc;
 }
 
-int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies, int nrep, const int* ik,
-                                int s_left, int s_right, unsigned long long seed, double* T_out,
-                                double* T_minus_out, int* rank_out, int* status_out, int* iters_out) {
-  if (!ctx) return TRANSEC_EINVAL;
-  if (!ctx->have_v || !ctx->have_abc || !ctx->have_k)
-    return ms_fail(ctx, TRANSEC_ESTATE, "potential, absorbing boundary and k-mesh must be set");
-  if (ne < 1 || ne > 1024 || nrep < 0 || !energies || (nrep > 0 && (!ik || !T_out)))
-    return ms_fail(ctx, TRANSEC_EINVAL, "bad sketch arguments (1 <= ne <= 1024)");
-  if (s_left < 1 || s_left > kGnMaxL || s_right < s_left || s_right > kGnMaxR)
-    return ms_fail(ctx, TRANSEC_EINVAL, "sketch sizes must satisfy 1 <= s_left <= 32, s_left <= s_right <= 64");
-  if (nrep == 0) return TRANSEC_OK;
-  for (int e = 0; e < ne; ++e)
-    if (!std::isfinite(energies[e])) return ms_fail(ctx, TRANSEC_EINVAL, "non-finite energy");
-  for (int r = 0; r < nrep; ++r)
-    if (ik[r] < 0 || ik[r] >= ctx->nk) return ms_fail(ctx, TRANSEC_EINVAL, "k index out of range");
-  if (ctx->rplanes.empty()) return ms_fail(ctx, TRANSEC_EINVAL, "right absorbing profile is zero everywhere");
-  DevScope ds(ctx->device);
-  MS_CK(cudaStreamSynchronize(ctx->user));
-  std::vector<double> es(energies, energies + ne), sorted = es;
-  std::sort(sorted.begin(), sorted.end());
-  const double e0 = sorted[ne / 2];
+// Full trace T(E, k), T(E, -k) of the k groups ik by the two-sided sketch, in the
+// context's precision.  Outputs [group][energy].
+int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vector<int>& ik, int s_left,
+                 int s_right, unsigned long long seed, SweepOut& out) {
+  const int ne = (int)es.size(), nrep = (int)ik.size();
   const int per = s_left + s_right;
   std::vector<MsItem> items;
   std::vector<int> run_slot((size_t)nrep * per);
@@ -1370,7 +1376,7 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
   if (!ctx->sweep) ctx->sweep = new SweepBufs();
   double* rt = nullptr;
   int *rit = nullptr, *rst = nullptr;
-  int rc = run_sweep(ctx, items, es, e0, S, nrep, std::max(s_left, s_right), seed, &rt, &rit, &rst);
+  int rc = run_sweep(ctx, items, es, seed_energy(es), S, nrep, std::max(s_left, s_right), seed, &rt, &rit, &rst);
   cudaFree(rt);
   cudaFree(rit);
   cudaFree(rst);
@@ -1423,11 +1429,8 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
   if (g0) cudaEventDestroy(g0);
   if (g1) cudaEventDestroy(g1);
   // seed iterations per group: the longest run of the group
-  std::vector<MsShift> hsh;
-  if (e == cudaSuccess && iters_out) {
-    hsh.resize((size_t)S * ne);
-    e = cudaMemcpy(hsh.data(), B.sh, hsh.size() * sizeof(MsShift), cudaMemcpyDeviceToHost);
-  }
+  std::vector<MsShift> hsh((size_t)S * ne);
+  if (e == cudaSuccess) e = cudaMemcpy(hsh.data(), B.sh, hsh.size() * sizeof(MsShift), cudaMemcpyDeviceToHost);
   cudaFree(d_rs);
   cudaFree(d_T);
   cudaFree(d_rank);
@@ -1436,23 +1439,182 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
     cudaGetLastError();
     return ms_fail(ctx, TRANSEC_ECUDA, std::string("sketch reduction: ") + cudaGetErrorString(e));
   }
-  int worst = TRANSEC_OK;
+  const size_t m = (size_t)nrep * ne;
+  out.t.resize(m);
+  out.tm.resize(m);
+  out.rank.resize(m);
+  out.st.resize(m);
+  out.it.resize(m);
   for (int r = 0; r < nrep; ++r)
     for (int s = 0; s < ne; ++s) {
       const size_t o = ((size_t)r * ne + s) * 2;
       const size_t u = (size_t)r * ne + s;
-      T_out[u] = T[o];
-      if (T_minus_out) T_minus_out[u] = T[o + 1];
-      if (rank_out) rank_out[u] = std::min(rk[o], rk[o + 1]);
-      const int w = ms_severity(stt[o]) >= ms_severity(stt[o + 1]) ? stt[o] : stt[o + 1];
-      if (status_out) status_out[u] = w;
-      if (ms_severity(w) > ms_severity(worst)) worst = w;
-      if (iters_out) {
-        int mx = 0;
-        for (int c = 0; c < per; ++c) mx = std::max(mx, hsh[(size_t)run_slot[(size_t)r * per + c] * ne + s].conv_it);
-        iters_out[u] = mx;
-      }
+      out.t[u] = T[o];
+      out.tm[u] = T[o + 1];
+      out.rank[u] = std::min(rk[o], rk[o + 1]);
+      out.st[u] = ms_severity(stt[o]) >= ms_severity(stt[o + 1]) ? stt[o] : stt[o + 1];
+      int mx = 0;
+      for (int c = 0; c < per; ++c) mx = std::max(mx, hsh[(size_t)run_slot[(size_t)r * per + c] * ne + s].conv_it);
+      out.it[u] = mx;
     }
+  return TRANSEC_OK;
+}
+
+bool redo_status(int st) { return st == TRANSEC_ENOCONV || st == TRANSEC_EBREAKDOWN; }
+
+// Energies (as indices into es) and rows (items or k groups) of a [row][energy] status
+// table that failed; empty when none did.
+void failed_parts(const std::vector<int>& st, int nrows, int ne, std::vector<int>& rows, std::vector<int>& cols) {
+  rows.clear();
+  cols.clear();
+  std::vector<char> ce(ne, 0);
+  for (int r = 0; r < nrows; ++r) {
+    bool any = false;
+    for (int s = 0; s < ne; ++s)
+      if (redo_status(st[(size_t)r * ne + s])) {
+        any = true;
+        ce[s] = 1;
+      }
+    if (any) rows.push_back(r);
+  }
+  for (int s = 0; s < ne; ++s)
+    if (ce[s]) cols.push_back(s);
+}
+
+// Runs f with the context's precision set to FP64, restoring it afterwards.
+template <typename F>
+int in_fp64(transec_ctx* ctx, F f) {
+  const int saved = ctx->opts.precision;
+  ctx->opts.precision = TRANSEC_PREC_FP64;
+  const int rc = f();
+  ctx->opts.precision = saved;
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, int nitems, const int* ik,
+                            const int64_t* cols, double* t_out, double* t_minus_out, int* iters_out,
+                            int* status_out) {
+  if (!ctx) return TRANSEC_EINVAL;
+  if (!ctx->have_v || !ctx->have_abc || !ctx->have_k)
+    return ms_fail(ctx, TRANSEC_ESTATE, "potential, absorbing boundary and k-mesh must be set");
+  if (ne < 1 || ne > 1024 || nitems < 0 || !energies || (nitems > 0 && (!ik || !cols || !t_out)))
+    return ms_fail(ctx, TRANSEC_EINVAL, "bad multi-shift arguments (1 <= ne <= 1024)");
+  if (nitems == 0) return TRANSEC_OK;
+  const long long nrhs = (long long)ctx->lplanes.size() * ctx->g.nxy;
+  for (int e = 0; e < ne; ++e)
+    if (!std::isfinite(energies[e])) return ms_fail(ctx, TRANSEC_EINVAL, "non-finite energy");
+  for (int i = 0; i < nitems; ++i) {
+    if (ik[i] < 0 || ik[i] >= ctx->nk) return ms_fail(ctx, TRANSEC_EINVAL, "k index out of range");
+    if (cols[i] < 0 || cols[i] >= nrhs) return ms_fail(ctx, TRANSEC_EINVAL, "column out of range");
+  }
+  if (ctx->rplanes.empty()) return ms_fail(ctx, TRANSEC_EINVAL, "right absorbing profile is zero everywhere");
+  DevScope ds(ctx->device);
+  MS_CK(cudaStreamSynchronize(ctx->user));
+  const std::vector<double> es(energies, energies + ne);
+  const std::vector<int> hik(ik, ik + nitems);
+  const std::vector<long long> hc(cols, cols + nitems);
+  SweepOut out;
+  int rc = columns_solve(ctx, es, hik, hc, out);
+  if (rc != TRANSEC_OK) return rc;
+  // double-float results that did not converge: the failed items again in FP64 at the
+  // energies that failed for any of them
+  std::vector<int> rows, ecols;
+  if (ctx->opts.precision == TRANSEC_PREC_DF64) failed_parts(out.st, nitems, ne, rows, ecols);
+  if (!rows.empty()) {
+    std::vector<double> e2;
+    std::vector<int> k2;
+    std::vector<long long> c2;
+    for (int s : ecols) e2.push_back(es[s]);
+    for (int r : rows) {
+      k2.push_back(hik[r]);
+      c2.push_back(hc[r]);
+    }
+    SweepOut o2;
+    rc = in_fp64(ctx, [&] { return columns_solve(ctx, e2, k2, c2, o2); });
+    if (rc != TRANSEC_OK) return rc;
+    for (size_t a = 0; a < rows.size(); ++a)
+      for (size_t b = 0; b < ecols.size(); ++b) {
+        const size_t u = (size_t)rows[a] * ne + ecols[b], v = a * ecols.size() + b;
+        if (!redo_status(out.st[u])) continue;
+        out.t[u] = o2.t[v];
+        out.tm[u] = o2.tm[v];
+        out.st[u] = o2.st[v];
+        out.it[u] += o2.it[v];
+        ctx->sweep_fp64_redone += 1;
+      }
+  }
+  int worst = TRANSEC_OK;
+  for (size_t u = 0; u < (size_t)nitems * ne; ++u) {
+    t_out[u] = out.t[u];
+    if (t_minus_out) t_minus_out[u] = out.tm[u];
+    if (iters_out) iters_out[u] = out.it[u];
+    if (status_out) status_out[u] = out.st[u];
+    if (ms_severity(out.st[u]) > ms_severity(worst)) worst = out.st[u];
+  }
+  if (worst != TRANSEC_OK) ctx->err = std::string("some columns failed: ") + transec_status_string(worst);
+  return worst;
+}
+
+int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies, int nrep, const int* ik,
+                                int s_left, int s_right, unsigned long long seed, double* T_out,
+                                double* T_minus_out, int* rank_out, int* status_out, int* iters_out) {
+  if (!ctx) return TRANSEC_EINVAL;
+  if (!ctx->have_v || !ctx->have_abc || !ctx->have_k)
+    return ms_fail(ctx, TRANSEC_ESTATE, "potential, absorbing boundary and k-mesh must be set");
+  if (ne < 1 || ne > 1024 || nrep < 0 || !energies || (nrep > 0 && (!ik || !T_out)))
+    return ms_fail(ctx, TRANSEC_EINVAL, "bad sketch arguments (1 <= ne <= 1024)");
+  if (s_left < 1 || s_left > kGnMaxL || s_right < s_left || s_right > kGnMaxR)
+    return ms_fail(ctx, TRANSEC_EINVAL, "sketch sizes must satisfy 1 <= s_left <= 32, s_left <= s_right <= 64");
+  if (nrep == 0) return TRANSEC_OK;
+  for (int e = 0; e < ne; ++e)
+    if (!std::isfinite(energies[e])) return ms_fail(ctx, TRANSEC_EINVAL, "non-finite energy");
+  for (int r = 0; r < nrep; ++r)
+    if (ik[r] < 0 || ik[r] >= ctx->nk) return ms_fail(ctx, TRANSEC_EINVAL, "k index out of range");
+  if (ctx->rplanes.empty()) return ms_fail(ctx, TRANSEC_EINVAL, "right absorbing profile is zero everywhere");
+  DevScope ds(ctx->device);
+  MS_CK(cudaStreamSynchronize(ctx->user));
+  const std::vector<double> es(energies, energies + ne);
+  const std::vector<int> hik(ik, ik + nrep);
+  SweepOut out;
+  int rc = sketch_solve(ctx, es, hik, s_left, s_right, seed, out);
+  if (rc != TRANSEC_OK) return rc;
+  // double-float results that did not converge: the failed k groups again with FP64
+  // runs at the energies that failed for any of them (a fresh random draw)
+  std::vector<int> rows, ecols;
+  if (ctx->opts.precision == TRANSEC_PREC_DF64) failed_parts(out.st, nrep, ne, rows, ecols);
+  if (!rows.empty()) {
+    std::vector<double> e2;
+    std::vector<int> k2;
+    for (int s : ecols) e2.push_back(es[s]);
+    for (int r : rows) k2.push_back(hik[r]);
+    SweepOut o2;
+    rc = in_fp64(ctx, [&] { return sketch_solve(ctx, e2, k2, s_left, s_right, seed ^ 0x5DEECE66DULL, o2); });
+    if (rc != TRANSEC_OK) return rc;
+    for (size_t a = 0; a < rows.size(); ++a)
+      for (size_t b = 0; b < ecols.size(); ++b) {
+        const size_t u = (size_t)rows[a] * ne + ecols[b], v = a * ecols.size() + b;
+        if (!redo_status(out.st[u])) continue;
+        out.t[u] = o2.t[v];
+        out.tm[u] = o2.tm[v];
+        out.rank[u] = o2.rank[v];
+        out.st[u] = o2.st[v];
+        out.it[u] += o2.it[v];
+        ctx->sweep_fp64_redone += 1;
+      }
+  }
+  int worst = TRANSEC_OK;
+  for (size_t u = 0; u < (size_t)nrep * ne; ++u) {
+    T_out[u] = out.t[u];
+    if (T_minus_out) T_minus_out[u] = out.tm[u];
+    if (rank_out) rank_out[u] = out.rank[u];
+    if (status_out) status_out[u] = out.st[u];
+    if (iters_out) iters_out[u] = out.it[u];
+    if (ms_severity(out.st[u]) > ms_severity(worst)) worst = out.st[u];
+  }
   if (worst != TRANSEC_OK) ctx->err = std::string("some (E, k) failed: ") + transec_status_string(worst);
   return worst;
 }

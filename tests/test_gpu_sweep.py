@@ -151,3 +151,31 @@ def test_sketch_unequal_spacings(precision):
     for s, e in enumerate(energies):
         tp, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf)
         assert abs(r["T"][0, s] - tp) <= TOL_T
+
+
+def test_double_float_results_that_stall_are_solved_again_in_fp64():
+    """A stall limit far too short makes every double-float run stop early: every
+    result then comes from the FP64 re-solve inside the same call, bit-identical to an
+    FP64 call for the unit columns, and counted in the stats."""
+    need_gpu()
+    kf = (0.21, -0.34)
+    inst = _inst(kf)
+    energies = np.linspace(0.2, 0.6, 5)
+    cols = np.array([5, 60, 200], np.int64)
+    ik = np.zeros(cols.size, np.int32)
+    with context(inst, precision=0) as tr:
+        ref = tr.shifted_columns(energies, ik, cols)
+        sk_ref = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=3)
+        tr.set_solver(precision=2, df_stall_its=5)
+        tr.stats_reset()
+        got = tr.shifted_columns(energies, ik, cols)
+        redone_cols = tr.sweep_stats()["fp64_redone"]
+        sk = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=3)
+        redone_all = tr.sweep_stats()["fp64_redone"]
+    assert np.all(ref["status"] == 0) and np.all(got["status"] == 0)
+    assert redone_cols == cols.size * energies.size
+    np.testing.assert_array_equal(got["t"], ref["t"])
+    np.testing.assert_array_equal(got["t_minus"], ref["t_minus"])
+    assert redone_all - redone_cols == energies.size
+    assert np.all(sk["status"] == 0)
+    assert np.abs(sk["T"] - sk_ref["T"]).max() <= TOL_T
