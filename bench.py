@@ -407,7 +407,7 @@ def run_sketch(args):
     prec = pkg.PREC_FP64 if args.form == "sketch_fp64" else pkg.PREC_DF64
     tr = pkg.Transec.from_instance(inst, device=local, tol=1e-10, precision=prec)
     e2e_steps = min(args.steps, 2)
-    plan = sketch_plan(len(inst.energies), reps, (args.warmup + args.steps + e2e_steps) * ws, W)
+    plan = sketch_plan(len(inst.energies), reps, (args.warmup + args.steps) * ws, W)
 
     def window(i):
         k, e0 = plan[i * ws + rank]
@@ -440,7 +440,11 @@ def run_sketch(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     clocks.start()
     ev0.record()
-    results = [step(args.warmup + i) for i in range(args.steps)]
+    results, step_s = [], []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        results.append(step(args.warmup + i))
+        step_s.append(round(time.perf_counter() - t0, 2))
     ev1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -459,15 +463,17 @@ def run_sketch(args):
     pm_diff = float(np.abs(T[ok] - Tm[ok]).max()) if ok.any() else None
 
     # end to end through the public API with host arrays: the window's energies and k in,
-    # T(E, +-k), ranks, statuses and iterations out, host wall clock
+    # T(E, +-k), ranks, statuses and iterations out, host wall clock; the same windows
+    # as the first timed steps, so that the two figures compare like with like
     e2e_s = 0.0
     for i in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        step(args.warmup + args.steps + i)
+        step(args.warmup + i)
         e2e_s += time.perf_counter() - t0
     e2e_s = replicas.max_over_ranks(e2e_s, device=dev)
     e2e_value = replicas.whole_job_rate(per_step * e2e_steps, ws, e2e_s)
+    same_steps_value = replicas.whole_job_rate(per_step * e2e_steps, ws, sum(step_s[:e2e_steps]))
 
     # parity against the plain FP64 arithmetic on the first timed window: the same sketch
     # in the FP64 engine (the double-float form's metric bar is |dT| <= 1e-6 vs FP64)
@@ -493,13 +499,19 @@ def run_sketch(args):
     k, en = window(0)
     tr.set_solver(profile=1, maxit=prof_its)
     tr.stats_reset()
+    pclk = Clocks(local)
+    pclk.start()
     tr.transmission_sketch(en, [k], s_left=sl, s_right=sr, seed=1)
+    prof_clk = pclk.stop()
     swp = tr.sweep_stats()
     tr.set_solver(profile=0, maxit=100000)
     runs = sl + sr
     ph_per_launch = runs * 2 * g.n  # every run active: both halves of every grid point
-    st_ms = swp["stencil_ms"] / max(1, swp["stencil_launches"])
-    sh_ms = swp["shift_ms"] / max(1, swp["shift_launches"])
+    # the kernels of the form being timed (a bounded pass ends its runs unconverged, and
+    # the double-float form then redoes them in FP64: those launches are counted apart)
+    key = "_df" if prec == pkg.PREC_DF64 else ""
+    st_ms = swp["stencil" + key + "_ms"] / max(1, swp["stencil" + key + "_launches"])
+    sh_ms = swp["shift" + key + "_ms"] / max(1, swp["shift" + key + "_launches"])
     peaks = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
     if prec == pkg.PREC_DF64:
@@ -534,6 +546,7 @@ def run_sketch(args):
                             "hbm_frac_of_measured": shift_bytes / (sh_ms / 1e3) / 1e9 / hbm_peak}
     roof["timing"] = (f"separate profiled pass: one window, {runs} runs x {W} shifts, {prof_its} iterations, "
                       "CUDA events around every stencil and shift-update launch on the context's stream")
+    roof["profile_clocks"] = prof_clk
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -552,6 +565,7 @@ def run_sketch(args):
             "mean_seed_iterations": float(its.mean()), "max_seed_iterations": int(its.max()),
             "failed_results": int((~ok).sum()), "max_abs_T_k_minus_T_mk": pm_diff,
             "results_redone_in_fp64": int(sw.get("fp64_redone", 0)),
+            "step_seconds": step_s,
             "min_rank": int(np.concatenate([r["rank"][0] for r in results]).min()),
             "parity_vs_fp64": parity,
             "l2": "per-step working set (36 runs x 2 halves x 192,000 points x 4 vectors x 16 B = 0.9 GB, plus "
@@ -560,7 +574,8 @@ def run_sketch(args):
         },
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": W * 8 + 4,
-                "d2h_bytes_per_step": W * (8 + 8 + 4 + 4 + 4)},
+                "d2h_bytes_per_step": W * (8 + 8 + 4 + 4 + 4),
+                "windows": f"the first {e2e_steps} timed windows again (their timed rate: {same_steps_value:.4g})"},
         "gpu_launches": int(st["launches"]),
         "clocks": clk,
     }

@@ -412,13 +412,16 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
  * Counters of the multi-shift engine since the last transec_stats_reset: seed
  * iterations summed over runs, per-shift point updates (kept points x halves x
  * iterations of each shift), with opts.profile set the event-timed stencil and
- * shifted-update kernels (ms, launches) and the sketch reduction (ms), and the
+ * shifted-update kernels (ms, launches) of the FP64 runs and, apart, of the
+ * double-float runs (the *_df outputs), and the sketch reduction (ms), and the
  * (energy, column or k) results of double-float calls that were solved again in FP64
  * (fp64_redone).  Any output may be NULL.
  */
 int transec_sweep_stats(const transec_ctx* ctx, long long* iters, long long* shift_points,
                         double* stencil_ms, long long* stencil_launches, double* shift_ms,
-                        long long* shift_launches, double* reduce_ms, long long* fp64_redone);
+                        long long* shift_launches, double* stencil_df_ms, long long* stencil_df_launches,
+                        double* shift_df_ms, long long* shift_df_launches, double* reduce_ms,
+                        long long* fp64_redone);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next
  * call on the same context. */

@@ -102,7 +102,9 @@ _SIGS = {
                                               _P, _P, _P, _P, _P]),
     "transec_sweep_stats": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
-                                      C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+                                      C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_longlong)]),
     "transec_unet_destroy": (None, [_P]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
@@ -530,8 +532,9 @@ def transec_transmission_sketch(ctx, energies, ik, s_left=16, s_right=32, seed=0
 
 def transec_sweep_stats(ctx) -> dict:
     v = [C.c_longlong(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(),
-         C.c_double(), C.c_longlong()]
+         C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong()]
     _check(ctx, load().transec_sweep_stats(ctx, *[C.byref(x) for x in v]), "transec_sweep_stats")
     keys = ("iters", "shift_points", "stencil_ms", "stencil_launches", "shift_ms", "shift_launches",
-            "reduce_ms", "fp64_redone")
+            "stencil_df_ms", "stencil_df_launches", "shift_df_ms", "shift_df_launches", "reduce_ms",
+            "fp64_redone")
     return {k: x.value for k, x in zip(keys, v)}

@@ -1438,13 +1438,21 @@ int transec_stats_reset(transec_ctx* ctx) {
   ctx->sweep_stencil_ms = ctx->sweep_shift_ms = ctx->sweep_update_ms = ctx->sweep_reduce_ms = 0;
   ctx->sweep_stencil_launches = ctx->sweep_shift_launches = 0;
   ctx->sweep_fp64_redone = 0;
+  ctx->sweep_stencil_df_ms = ctx->sweep_shift_df_ms = 0;
+  ctx->sweep_stencil_df_launches = ctx->sweep_shift_df_launches = 0;
   return TRANSEC_OK;
 }
 
 int transec_sweep_stats(const transec_ctx* ctx, long long* iters, long long* shift_points,
                         double* stencil_ms, long long* stencil_launches, double* shift_ms,
-                        long long* shift_launches, double* reduce_ms, long long* fp64_redone) {
+                        long long* shift_launches, double* stencil_df_ms, long long* stencil_df_launches,
+                        double* shift_df_ms, long long* shift_df_launches, double* reduce_ms,
+                        long long* fp64_redone) {
   if (!ctx) return TRANSEC_EINVAL;
+  if (stencil_df_ms) *stencil_df_ms = ctx->sweep_stencil_df_ms;
+  if (stencil_df_launches) *stencil_df_launches = ctx->sweep_stencil_df_launches;
+  if (shift_df_ms) *shift_df_ms = ctx->sweep_shift_df_ms;
+  if (shift_df_launches) *shift_df_launches = ctx->sweep_shift_df_launches;
   if (fp64_redone) *fp64_redone = ctx->sweep_fp64_redone;
   if (iters) *iters = ctx->sweep_iters;
   if (shift_points) *shift_points = ctx->sweep_shift_points;

@@ -1248,12 +1248,12 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
       for (int i = 0; i < C; ++i) {
         float t0 = 0.f, t1 = 0.f;
         if (cudaEventElapsedTime(&t0, ctx->prof_ev[4 * i], ctx->prof_ev[4 * i + 1]) == cudaSuccess) {
-          ctx->sweep_stencil_ms += t0;
-          ctx->sweep_stencil_launches += 1;
+          (dfm ? ctx->sweep_stencil_df_ms : ctx->sweep_stencil_ms) += t0;
+          (dfm ? ctx->sweep_stencil_df_launches : ctx->sweep_stencil_launches) += 1;
         }
         if (cudaEventElapsedTime(&t1, ctx->prof_ev[4 * i + 2], ctx->prof_ev[4 * i + 3]) == cudaSuccess) {
-          ctx->sweep_shift_ms += t1;
-          ctx->sweep_shift_launches += 1;
+          (dfm ? ctx->sweep_shift_df_ms : ctx->sweep_shift_ms) += t1;
+          (dfm ? ctx->sweep_shift_df_launches : ctx->sweep_shift_launches) += 1;
         }
       }
       cudaGetLastError();
