@@ -53,3 +53,30 @@ def test_cu_bulk_sampled_columns(precision, slots):
     err_m = np.abs(r["t_minus"] - tm)
     assert err_p.max() <= TOL_COL, err_p
     assert err_m.max() <= TOL_COL, err_m
+
+
+@pytest.mark.parametrize("precision", [0, 2])
+def test_cu_bulk_golden_columns_through_energy_windows(precision):
+    """The multi-shift engine on the full-size columns: each golden energy is the last
+    energy of a three-energy window (so it is a shift of the run, not its seed), the
+    three columns of that energy in one call; every t_j at k and -k within the per-column
+    bar, in FP64 and in double-float."""
+    need_gpu()
+    items = _golden()
+    inst = cu_bulk()
+    de = float(inst.energies[1] - inst.energies[0])
+    by_e = {}
+    for it in items:
+        by_e.setdefault(it["e_index"], []).append(it)
+    with context(inst, precision=precision, tol=1e-10, maxit=60000) as tr:
+        for ei, group in sorted(by_e.items()):
+            e = inst.energies[ei]
+            window = np.array([e - 2 * de, e - de, e])
+            ik = np.array([it["ik"] for it in group], np.int32)
+            cols = np.array([it["col"] for it in group], np.int64)
+            r = tr.shifted_columns(window, ik, cols)
+            assert np.all(r["status"] == 0), (ei, r["status"])
+            tp = np.array([it["t"] for it in group])
+            tm = np.array([it["t_minus"] for it in group])
+            assert np.abs(r["t"][:, 2] - tp).max() <= TOL_COL, (ei, r["t"][:, 2], tp)
+            assert np.abs(r["t_minus"][:, 2] - tm).max() <= TOL_COL, (ei, r["t_minus"][:, 2], tm)
