@@ -56,9 +56,10 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.070e9 * 2 / 1e12
 # FP32 pipe roofline of the double-float stencil, in FP32 operations (add, multiply or
 # FMA, one each): 128 FP32 lanes per SM x 152 SMs x 2070 MHz
 FP32_OPS_PEAK_T = 128 * 152 * 2.070e9 / 1e12
-# DRAM bytes per point-half of one double-float stencil launch (ncu capture in
-# profiles/k_stencil_df_cu_bulk.md); None until captured for the current kernel
-DF_STENCIL_DRAM_PER_POINT_HALF = None
+# DRAM bytes per point-half of one double-float stencil launch, from the ncu capture in
+# profiles/k_stencil_df_cu_bulk.md (929.6 MB for 13.824 M point-halves); reset to None
+# whenever the kernel changes
+DF_STENCIL_DRAM_PER_POINT_HALF = 929.6e6 / 13.824e6
 
 
 def stencil_flops_per_point(order: int) -> int:
