@@ -42,6 +42,9 @@ METRIC = "converged (E,k) T(E) solves/sec at |ΔT|≤1e-6 vs plain FP64 GPU; ste
 UNIT = "(E,k) solves/s"
 WORKLOAD = ("bulk fcc Cu [001] a=6.82, 20x20x480 h=0.341, order 12, V0=1.2 sigma=0.9 +-2% "
             "jitter, 64-plane CAPs 0.3 Ha, 8x8 MP k-mesh, 256 energies in E_F+-0.3 Ha, tol 1e-10")
+WORKLOAD_IDEAL = ("ideal bulk fcc Cu [001] (no jitter, V invariant under the in-plane inversion about an "
+                  "atom), otherwise as the bulk Cu workload: 20x20x480 h=0.341, order 12, 64-plane CAPs 0.3 Ha, "
+                  "8x8 MP k-mesh, 256 energies in E_F+-0.3 Ha, tol 1e-10")
 WORKLOAD_RH = ("Rh periodic point contact [001] a=7.18, 3x3 cells, 60x60x512 h=0.359, order 12, "
                "V0=1.4 sigma=0.95, hyperboloid neck r0=4, 1% vacancies, 64-plane CAPs 0.3 Ha, "
                "4x4 MP k-mesh, 512 energies in E_F+-0.3 Ha, tol 1e-10")
@@ -395,18 +398,21 @@ def run_sketch(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    from workloads import cu_bulk, rh_point_contact
+    from workloads import cu_bulk, cu_bulk_ideal, rh_point_contact
     import paper_2208_02783_gb300 as pkg
     from paper_2208_02783_gb300 import build, replicas
 
     pkg.load(build.build())
     rh = args.workload == "rh_point_contact"
-    inst = rh_point_contact() if rh else cu_bulk()
+    ideal = args.workload == "cu_bulk_ideal"
+    inst = rh_point_contact() if rh else (cu_bulk_ideal() if ideal else cu_bulk())
     g = inst.grid
     reps = k_representatives(inst.kfrac)
     W, sl, sr = args.window, args.s_left, args.s_right
     prec = pkg.PREC_FP64 if args.form == "sketch_fp64" else pkg.PREC_DF64
-    tr = pkg.Transec.from_instance(inst, device=local, tol=1e-10, precision=prec)
+    psym = 1 if args.psym else 0
+    H = 1 if psym else 2  # halves per run
+    tr = pkg.Transec.from_instance(inst, device=local, tol=1e-10, precision=prec, psym=psym)
     e2e_steps = min(args.steps, 2)
     plan = sketch_plan(len(inst.energies), reps, (args.warmup + args.steps) * ws, W)
 
@@ -481,9 +487,9 @@ def run_sketch(args):
     parity = None
     if rank == 0 and prec == pkg.PREC_DF64 and not args.no_parity:
         k, en = window(args.warmup)
-        tr.set_solver(precision=pkg.PREC_FP64)
+        tr.set_solver(precision=pkg.PREC_FP64, psym=0)
         ref = tr.transmission_sketch(en, [k], s_left=sl, s_right=sr, seed=1000 + args.warmup)
-        tr.set_solver(precision=prec)
+        tr.set_solver(precision=prec, psym=psym)
         got = results[0]
         okp = (ref["status"][0] == 0) & (got["status"][0] == 0)
         parity = {"window_energies": W, "k_index": k,
@@ -507,7 +513,7 @@ def run_sketch(args):
     swp = tr.sweep_stats()
     tr.set_solver(profile=0, maxit=100000)
     runs = sl + sr
-    ph_per_launch = runs * 2 * g.n  # every run active: both halves of every grid point
+    ph_per_launch = runs * H * g.n  # every run active: every half of every grid point
     # the kernels of the form being timed (a bounded pass ends its runs unconverged, and
     # the double-float form then redoes them in FP64: those launches are counted apart)
     key = "_df" if prec == pkg.PREC_DF64 else ""
@@ -541,7 +547,7 @@ def run_sketch(args):
                 "per_launch": {"point_halves": ph_per_launch, "flops": flops, "ms": st_ms},
                 "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
     no = max(int(np.count_nonzero(inst.gamma_l)), int(np.count_nonzero(inst.gamma_r))) * g.nxy
-    shift_bytes = runs * W * 2 * no * 64  # read/write p_sigma and x_sigma, 16 B each, per shift and half
+    shift_bytes = runs * W * H * no * 64  # read/write p_sigma and x_sigma, 16 B each, per shift and half
     roof["shift_kernel"] = {"ms": sh_ms, "bytes_per_launch": shift_bytes,
                             "hbm_gbs": shift_bytes / (sh_ms / 1e3) / 1e9,
                             "hbm_frac_of_measured": shift_bytes / (sh_ms / 1e3) / 1e9 / hbm_peak}
@@ -555,9 +561,11 @@ def run_sketch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "df64+f64" if prec == pkg.PREC_DF64 else "c128",
         "data": "synthetic",
         "config": {
-            "workload": WORKLOAD_RH if rh else WORKLOAD,
+            "workload": WORKLOAD_RH if rh else (WORKLOAD_IDEAL if ideal else WORKLOAD),
             "form": ("full trace T(E, +-k) from a two-sided randomized sketch of Gamma_R^1/2 G Gamma_L^1/2: "
-                     f"{sl} left + {sr} right random right-hand sides, each a multi-shift transpose BiCG over "
+                     f"{sl} left + {sr} right random right-hand sides, each a multi-shift "
+                     + ("P-symmetric COCG (one operator application per iteration)" if psym else "transpose BiCG")
+                     + " over "
                      f"a window of {W} energies, " + ("double-float vectors and stencil, FP64 scalars"
                                                       if prec == pkg.PREC_DF64 else "FP64")),
             "step": f"one seeded k-pair x {W} consecutive energies (seeded position) = {per_step} (E, k) values",
@@ -569,8 +577,8 @@ def run_sketch(args):
             "step_seconds": step_s,
             "min_rank": int(np.concatenate([r["rank"][0] for r in results]).min()),
             "parity_vs_fp64": parity,
-            "l2": "per-step working set (36 runs x 2 halves x 192,000 points x 4 vectors x 16 B = 0.9 GB, plus "
-                  "the per-shift planes) exceeds L2; no flush needed",
+            "l2": f"per-step working set ({runs} runs x {H} halves x {g.n:,} points x 4 vectors x 16 B = "
+                  f"{runs * H * g.n * 64 / 1e9:.2g} GB, plus the per-shift planes) exceeds L2; no flush needed",
             "sampling": "steps draw (k-pair, window position) from a seeded generator; ranks take disjoint steps",
         },
         "roofline": roof,
@@ -580,7 +588,9 @@ def run_sketch(args):
         "gpu_launches": int(st["launches"]),
         "clocks": clk,
     }
-    if rank == 0 and not args.no_cpu_baseline:
+    # (the oracle's iteration basis is the jittered bulk Cu workload's golden columns: no
+    # CPU figure is printed for the ideal cell)
+    if rank == 0 and not args.no_cpu_baseline and not ideal:
         mean_its = golden_mean_iterations()
         items = draw_items(inst, reps, inst.n_rhs, 64, 7000)
         with OraclePool("rh_point_contact" if rh else "cu_bulk") as op:
@@ -750,8 +760,10 @@ def main():
     ap.add_argument("--profile-case", action="store_true",
                     help="small bounded run for ncu: 32 columns, 40 iterations each (with "
                          "--workload learned: 3 forwards and 2 training steps), then exit")
+    ap.add_argument("--psym", action="store_true",
+                    help="sketch forms: P-symmetric COCG runs (needs --workload cu_bulk_ideal)")
     ap.add_argument("--workload", default="cu_bulk",
-                    choices=["cu_bulk", "rh_point_contact", "uneven_batch", "learned"],
+                    choices=["cu_bulk", "cu_bulk_ideal", "rh_point_contact", "uneven_batch", "learned"],
                     help="rh_point_contact: the 60x60x512 Rh point contact (use --items 16); "
                          "uneven_batch: the 96-cell mixed batch, batched vs looped per cell; "
                          "learned: the U-Net preconditioner's forward and FGMRES gain")

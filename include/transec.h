@@ -88,7 +88,7 @@ typedef struct transec_solver_opts {
                          iteration once its residual has dropped by this factor (or
                          has stalled); default 1e-5 */
   int tile_y;         /* stencil tile rows (0 = autotune); tiles span min(nx, 32) */
-  int slab;           /* z-planes per stencil block (0 = autotune) */
+  int slab;           /* most z-planes per stencil block; the depth used splits nz into equal slabs (0 = default) */
   int profile;        /* != 0: time every stencil and update launch with CUDA events on
                          the context's stream (read back with transec_stats) */
   int mixed_maxit;    /* mixed precision: FP32 iterations a column may take before it is
@@ -107,6 +107,14 @@ typedef struct transec_solver_opts {
                          first convergence, or 3x this from the start), its remaining
                          shifts stop and are solved again in FP64; default 8000,
                          negative = never */
+  int psym;           /* != 0: transec_transmission_sketch runs P-symmetric COCG instead
+                         of transpose BiCG (Sec. II.C: with V invariant under the in-plane
+                         rotation R_{z,pi} about grid point (0, 0), A(E, k)^T = P_k A(E, k)
+                         P_k^-1 for the Bloch-phased inversion P_k, so one operator
+                         application per iteration serves both k and -k).  Requires
+                         precision = TRANSEC_PREC_DF64, a potential that passes the
+                         inversion check of transec_set_potential, nx <= 32 and
+                         nx * ny <= 896; other entry points ignore it.  Default 0 */
 } transec_solver_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -399,7 +407,13 @@ int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, in
  * nrep * (s_left + s_right) runs are in flight at once (no refill).  With
  * opts.precision = TRANSEC_PREC_DF64 the runs are double-float, and the (k, energy)
  * results that do not converge that way (or stop under opts.df_stall_its) are
- * computed again with FP64 runs within the call.  Host arrays.
+ * computed again with FP64 runs within the call.  With opts.psym set the runs are
+ * P-symmetric COCG (one half each): Y and W at +k come from the primal solutions and
+ * their images under P_k (test vectors P_k psi for W), the -k pair from the same data
+ * mirrored, so T_minus equals T to rounding and is no independent estimate; EINVAL
+ * when opts.psym is set with another precision, a potential that is not
+ * inversion-symmetric (relative gap above 1e-12) or a plane too large for one tile.
+ * The FP64 re-solve of failed results uses transpose BiCG.  Host arrays.
  * Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT; per-result ENOCONV / EBREAKDOWN with
  * T = NaN.
  */

@@ -87,3 +87,22 @@ def system_matrix(g, v, gamma_l, gamma_r, energy, kfrac) -> sp.csr_matrix:
     gam = gamma_points(g, gamma_l) + gamma_points(g, gamma_r)
     d = sp.diags(energy + 1j * gam)
     return (d - h).tocsr()
+
+
+def inversion(g, kfrac) -> sp.csr_matrix:
+    """P_k: the in-plane rotation R_{z,pi} (x, y, z) -> (-x, -y, z) about grid point
+    (0, 0) acting on k-Bloch cell vectors (paper Sec. II.C, the C2 symmetry about z).
+
+    (P_k u)(x, y, z) = u(-x, -y, z); a mirrored coordinate -i outside the cell is
+    brought back by the Bloch condition u(i - nx) = exp(-i k_a L_a) u(i), so
+    (P_k)_{n, m} = exp(-2 pi i (ka [i > 0] + kb [j > 0])) with m the point
+    ((nx - i) mod nx, (ny - j) mod ny, l).  P_k is symmetric, and P_{-k} P_k = 1.
+    When V(x, y, z) = V(-x, -y, z), A(E, k)^T = P_k A(E, k) P_{-k}.
+    """
+    ka, kb = float(kfrac[0]), float(kfrac[1])
+    n, i, j, l = _indices(g)
+    im = np.where(i > 0, g.nx - i, 0)
+    jm = np.where(j > 0, g.ny - j, 0)
+    m = im + g.nx * (jm + g.ny * l)
+    ph = np.exp(-2j * np.pi * (ka * (i > 0) + kb * (j > 0)))
+    return sp.csr_matrix((ph, (n, m)), shape=(g.n, g.n))

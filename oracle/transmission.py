@@ -172,6 +172,44 @@ def bicg_transpose(a, b, tol, maxit, mark_tol=None):
     return x, y, its
 
 
+def cocg_psym(a, pk, b, tol, maxit):
+    """COCG for a P-symmetric A (paper Sec. II.C): A^T P = P A with P symmetric makes
+    P A complex symmetric, so CG runs with the bilinear form [u, v] = u^T P v.
+
+    This is BiCG whose shadow residual is P r (A^T P r = P A r keeps it so), with one
+    product with A per iteration.  Columns of ``b`` are solved independently; a column
+    stops once ||r||_2 <= tol ||b||_2 (||P r|| = ||r|| for the unitary P_k of
+    ``oracle.hamiltonian.inversion``).  Returns (x, iterations; negative where maxit
+    was reached).
+    """
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rho = np.einsum("ij,ij->j", pk @ r, r)
+    nb = np.linalg.norm(b, axis=0)
+    its = np.full(b.shape[1], -maxit)
+    live = np.ones(b.shape[1], bool)
+    for it in range(1, maxit + 1):
+        L = live
+        q = a @ p[:, L]
+        alpha = rho[L] / np.einsum("ij,ij->j", pk @ p[:, L], q)
+        x[:, L] += alpha * p[:, L]
+        r[:, L] -= alpha * q
+        rn = np.linalg.norm(r[:, L], axis=0)
+        done = rn <= tol * nb[L]
+        idx = np.nonzero(L)[0]
+        its[idx[done]] = it
+        live = L.copy()
+        live[idx[done]] = False
+        if not live.any():
+            break
+        rho_new = np.einsum("ij,ij->j", pk @ r[:, live], r[:, live])
+        beta = rho_new / rho[live]
+        p[:, live] = r[:, live] + beta * p[:, live]
+        rho[live] = rho_new
+    return x, its
+
+
 def is_real_phase(kfrac) -> bool:
     """True when exp(2 pi i kappa) is real on both axes (kappa in {0, 1/2} mod 1):
     then H_k is real symmetric and A is complex symmetric."""

@@ -50,6 +50,7 @@ class SolverOpts(C.Structure):
         ("mixed_decade_its", C.c_int),
         ("host_loop", C.c_int),
         ("df_stall_its", C.c_int),
+        ("psym", C.c_int),
     ]
 
 

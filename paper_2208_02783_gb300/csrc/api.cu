@@ -162,6 +162,10 @@ TileShape choose_tiles(const Geometry& g, int H, int elem_bytes, int max_threads
   t.D = slab > 0 ? slab : (elem_bytes >= 16 ? 32 : 64);
   t.D = std::min(t.D, g.nz);
   t.nslab = (g.nz + t.D - 1) / t.D;
+  // the requested depth is an upper bound: slabs of equal depth keep the blocks of a
+  // launch equally long (480 planes at depth 64 become 8 slabs of 60, not 7 of 64 and
+  // one of 32)
+  t.D = (g.nz + t.nslab - 1) / t.nslab;
   t.threads = ((t.TX * t.TY * H + 31) / 32) * 32;
   t.smem = (size_t)H * (t.TX + 2 * R) * (t.TY + 2 * R) * elem_bytes;
   return t;
@@ -804,6 +808,23 @@ __global__ void k_count_nonfinite(const double* a, long long n, int* bad) {
        i += (long long)gridDim.x * blockDim.x)
     if (!isfinite(a[i])) atomicAdd(bad, 1);
 }
+// out[0] = max |V(x, y, z) - V(-x mod nx, -y mod ny, z)|, out[1] = max |V|, as the bit
+// patterns of non-negative doubles (which order like the values)
+__global__ void k_inversion_gap(const double* v, int nx, int ny, long long n, unsigned long long* out) {
+  const long long nxy = (long long)nx * ny;
+  double gap = 0.0, mx = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long z = i / nxy;
+    const int w = (int)(i - z * nxy);
+    const int y = w / nx, x = w - y * nx;
+    const long long im = z * nxy + (x ? nx - x : 0) + (long long)nx * (y ? ny - y : 0);
+    gap = fmax(gap, fabs(v[i] - v[im]));
+    mx = fmax(mx, fabs(v[i]));
+  }
+  atomicMax(out, (unsigned long long)__double_as_longlong(gap));
+  atomicMax(out + 1, (unsigned long long)__double_as_longlong(mx));
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------------
@@ -890,15 +911,23 @@ int transec_set_potential(transec_ctx* ctx, const double* v_ks, int on_device) {
   CK(cudaMemsetAsync(bad.p, 0, sizeof(int), ctx->s));
   k_count_nonfinite<<<256, 256, 0, ctx->s>>>(ctx->d_v, n, (int*)bad.p);
   k_to_float<<<1024, 256, 0, ctx->s>>>(ctx->d_v, ctx->d_v32, n);
+  DevBuf gapb;
+  CK(cudaMalloc(&gapb.p, 2 * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(gapb.p, 0, 2 * sizeof(unsigned long long), ctx->s));
+  k_inversion_gap<<<256, 256, 0, ctx->s>>>(ctx->d_v, ctx->g.nx, ctx->g.ny, n, (unsigned long long*)gapb.p);
   CHECK_LAUNCH();
   int hbad = 0;
+  double hgap[2] = {0.0, 0.0};
   CK(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->s));
+  CK(cudaMemcpyAsync(hgap, gapb.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
   rc = end_call(ctx);
   if (rc) return rc;
   if (hbad) {
     ctx->have_v = false;
+    ctx->v_inversion_gap = std::nan("");
     return fail(ctx, TRANSEC_EINVAL, "v_ks holds non-finite values");
   }
+  ctx->v_inversion_gap = hgap[1] > 0.0 ? hgap[0] / hgap[1] : 0.0;
   ctx->have_v = true;
   return TRANSEC_OK;
 }
@@ -995,6 +1024,7 @@ int transec_set_solver(transec_ctx* ctx, const transec_solver_opts* opts) {
   transec_solver_opts o = *opts;
   if (o.method < 0 || o.method > 2 || o.precision < 0 || o.precision > 2 || o.tol < 0 ||
       o.maxit < 0 || o.slots < 0 || o.chunk < 0 || o.tile_y < 0 || o.slab < 0 || o.mixed_maxit < 0 ||
+      o.psym < 0 || o.psym > 1 ||
       !std::isfinite(o.tol) || !std::isfinite(o.reliable))
     return fail(ctx, TRANSEC_EINVAL, "invalid solver options");
   default_opts(&o);

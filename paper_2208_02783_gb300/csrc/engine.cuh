@@ -62,6 +62,9 @@ struct transec_ctx {
   double* d_v = nullptr;
   float* d_v32 = nullptr;
   bool have_v = false;
+  // max |V(x, y, z) - V(-x, -y, z)| / max |V| over the cell (in-plane inversion about
+  // grid point (0, 0), coordinates taken modulo the cell); NaN before a potential is set
+  double v_inversion_gap = __builtin_nan("");
   std::vector<double> gl, gr;
   double* d_gl = nullptr;
   double* d_gr = nullptr;

@@ -34,6 +34,7 @@ struct StencilDfArgs {
   int nx, ny, nz;
   long long nxy, n;
   int H, TX, TY, D, ntx, conj;
+  int psym;               // H = 1 and the plane in one tile: <p~, A p> = (P_k p)^T A p
   long long slot_stride;
 };
 
@@ -222,8 +223,18 @@ __global__ void __launch_bounds__(kDfThreads, 1) k_stencil_df(const StencilDfArg
       const dfc acc = dfc{dre.value(), dim_.value()};
       q[off] = dfc_store(acc);
       pout[off] = dfc_store(c);
-      // pairing form: half h pairs with half 1-h at the same point (or itself)
-      const dfc o = (a.H == 2) ? dfc_load(sm[(1 - half) * SW * SHt + (ty + R) * SW + tx + R]) : c;
+      // pairing form: half h pairs with half 1-h at the same point (or itself); the
+      // P-symmetric form pairs p with P_k p, its in-plane inversion about grid point
+      // (0, 0) with the Bloch factor exp(-i k_a L_a) of each axis whose mirror wraps
+      dfc o = c;
+      if (a.H == 2) {
+        o = dfc_load(sm[(1 - half) * SW * SHt + (ty + R) * SW + tx + R]);
+      } else if (a.psym) {
+        const int mx = gx ? nx - gx : 0, my_ = gy ? ny - gy : 0;
+        o = dfc_load(my[(my_ + R) * SW + mx + R]);
+        if (gx) o = dfc_mul(o, dfc_load(ph[kPhaseW - 1]));
+        if (gy) o = dfc_mul(o, dfc_load(ph[kPhaseN + kPhaseW - 1]));
+      }
       dfc_dot_add(sg_re, sg_im, dfc{df_scale(o.re, sc), df_scale(o.im, sc)},
                   dfc{df_scale(acc.re, sc), df_scale(acc.im, sc)});
     }
@@ -297,6 +308,79 @@ __global__ void __launch_bounds__(256) k_update_df(const UpdateDfArgs a) {
   const double rscale = (a.H == 2 ? 2.0 : 1.0) * unscale;
   double v4[4] = {rscale * df_value(rr_re.value()), rscale * df_value(rr_im.value()), unscale * (double)n0,
                   unscale * (double)n1};
+  block_sum<4>(v4, red);
+  if (threadIdx.x == 0) {
+    double* o = a.rho_part + ((size_t)slot * gridDim.x + blockIdx.x) * 4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[k] = v4[k];
+  }
+}
+
+// The P-symmetric form (H = 1): r -= alpha q, rho' = (P_k r)^T r and ||r||^2.  P_k
+// pairs a point with its in-plane mirror (same plane), so a thread updates both points
+// of a pair (the lower index owns it) and adds 2 phi r_i r_mirror (phi r_i^2 at a point
+// that is its own mirror).  grid (blocks, slots), 256 threads
+struct UpdateDfPsymArgs {
+  float4* r;
+  const float4* q;
+  const double* sig_part;  // [slot][sig_nblk][2]
+  int sig_nblk;
+  double* rho_part;        // [slot][gridDim.x][4]: rho re, rho im, |r|^2, |r|^2
+  const Slot* slots;
+  const int* escale;
+  const float4* phase;     // [nk][2][2][kPhaseN] Bloch phases, complex df64
+  int nx, ny;
+  long long nxy, n, slot_stride;
+};
+
+__global__ void __launch_bounds__(256) k_update_df_psym(const UpdateDfPsymArgs a) {
+  __shared__ double red[4][32];
+  __shared__ double2 s_alpha;
+  const int slot = blockIdx.y;
+  const Slot* stp = a.slots + slot;
+  if (stp->status != SLOT_ACTIVE) return;
+  if (threadIdx.x < 32) {
+    const double2 al = slot_alpha(a.sig_part + (size_t)slot * a.sig_nblk * 2, a.sig_nblk, stp->rho);
+    if (threadIdx.x == 0) s_alpha = al;
+  }
+  __syncthreads();
+  const dfc mal = dfc{df_split(-s_alpha.x), df_split(-s_alpha.y)};
+  const int ks = a.escale[slot];
+  const float sc = pow2f(ks);
+  const float4* ph = a.phase + (size_t)(stp->ik * 2) * 2 * kPhaseN;
+  const dfc phx = dfc_load(ph[kPhaseW - 1]), phy = dfc_load(ph[kPhaseN + kPhaseW - 1]);
+  const long long base = (long long)slot * a.slot_stride;
+  const int nx = a.nx, ny = a.ny;
+  dfacc rr_re, rr_im;
+  float n0 = 0.f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long z = i / a.nxy;
+    const int w = (int)(i - z * a.nxy);
+    const int y = w / nx, x = w - y * nx;
+    const long long im = z * a.nxy + (x ? nx - x : 0) + (long long)nx * (y ? ny - y : 0);
+    if (im < i) continue;
+    const dfc rv = dfc_fma(mal, dfc_load(a.q[base + i]), dfc_load(a.r[base + i]));
+    a.r[base + i] = dfc_store(rv);
+    const dfc s0 = dfc{df_scale(rv.re, sc), df_scale(rv.im, sc)};
+    n0 = __fmaf_rn(s0.re.hi, s0.re.hi, __fmaf_rn(s0.im.hi, s0.im.hi, n0));
+    dfc t = s0;
+    if (x) t = dfc_mul(t, phx);
+    if (y) t = dfc_mul(t, phy);
+    if (im == i) {
+      dfc_dot_add(rr_re, rr_im, t, s0);
+    } else {
+      const dfc rm = dfc_fma(mal, dfc_load(a.q[base + im]), dfc_load(a.r[base + im]));
+      a.r[base + im] = dfc_store(rm);
+      const dfc s1 = dfc{df_scale(rm.re, sc), df_scale(rm.im, sc)};
+      n0 = __fmaf_rn(s1.re.hi, s1.re.hi, __fmaf_rn(s1.im.hi, s1.im.hi, n0));
+      // phi r_i r_m + phi r_m r_i (the phase of a pair is the same from either end)
+      dfc_dot_add(rr_re, rr_im, dfc{df_scale(t.re, 2.f), df_scale(t.im, 2.f)}, s1);
+    }
+  }
+  const double unscale = ldexp(1.0, -2 * max(-126, min(126, ks)));
+  double v4[4] = {unscale * df_value(rr_re.value()), unscale * df_value(rr_im.value()), unscale * (double)n0,
+                  unscale * (double)n0};
   block_sum<4>(v4, red);
   if (threadIdx.x == 0) {
     double* o = a.rho_part + ((size_t)slot * gridDim.x + blockIdx.x) * 4;

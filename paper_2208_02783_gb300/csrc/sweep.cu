@@ -53,6 +53,10 @@ namespace transec {
 
 enum RunKind : int { RUN_UNIT = 0, RUN_LEFT = 1, RUN_RIGHT = 2 };
 
+// Largest relative inversion gap of V (max |V(r) - V(R_{z,pi} r)| / max |V|) accepted for
+// P-symmetric runs: the operator's own rounding, far below what moves T at 1e-6.
+constexpr double kPsymTol = 1e-12;
+
 // Per-run state beside the seed's Slot.
 struct MsSlot {
   double2 alpha;       // alpha_n of the current iteration
@@ -216,6 +220,10 @@ struct MsArgs {
   int maxit;
   int stall_its;           // > 0: a run stops once no shift has converged for this long
   int* escale;             // [S]
+  int H;                   // halves per run: 2 (transpose BiCG), 1 (P-symmetric COCG)
+  int psym;                // P-symmetric form: the bilinear forms pair r with P_k r
+  int nx, ny;
+  const double2* phase;    // [nk][2][2][kPhaseN] Bloch phases
   // UNIT results: [item][shift][2] t, [item][shift] iterations and status
   double* res_t;
   int* res_it;
@@ -259,7 +267,7 @@ __global__ void k_ms_assign(const MsArgs a) {
   q->next = next;
 }
 
-// r = b on both halves, p = 0, for newly assigned slots.  grid (blocks, S)
+// r = b on every half, p = 0, for newly assigned slots.  grid (blocks, S)
 template <typename V>
 __global__ void __launch_bounds__(256) k_ms_init(const MsArgs a) {
   V* R = reinterpret_cast<V*>(a.R);
@@ -292,8 +300,8 @@ __global__ void __launch_bounds__(256) k_ms_init(const MsArgs a) {
         b = make_double2(s * o.x, s * o.y);
       }
     }
-    for (int h = 0; h < 2; ++h) {
-      const long long off = (long long)slot * 2 * a.n + (long long)h * a.n + i;
+    for (int h = 0; h < a.H; ++h) {
+      const long long off = (long long)slot * a.H * a.n + (long long)h * a.n + i;
       vstore(R, off, b);
       vstore(P0, off, make_double2(0.0, 0.0));
     }
@@ -321,8 +329,8 @@ __global__ void __launch_bounds__(256) k_ms_init_shift(const MsArgs a) {
   }
 }
 
-// rho_0 = 2 b.b (pairing form of the two equal halves) and ||b|| of new random runs.
-// grid S, 256 threads
+// rho_0 = 2 b.b (pairing form of the two equal halves; (P_k b)^T b in the P-symmetric
+// form) and ||b|| of new random runs.  grid S, 256 threads
 template <typename V>
 __global__ void __launch_bounds__(256) k_ms_rho0(const MsArgs a) {
   __shared__ double red[3][32];
@@ -333,17 +341,28 @@ __global__ void __launch_bounds__(256) k_ms_rho0(const MsArgs a) {
   if (m.kind == RUN_UNIT) return;
   const int* planes = m.kind == RUN_LEFT ? a.lplanes : a.rplanes;
   const long long np = (long long)(m.kind == RUN_LEFT ? a.nlp : a.nrp) * a.nxy;
-  const V* r = reinterpret_cast<const V*>(a.R) + (long long)slot * 2 * a.n;
+  const V* r = reinterpret_cast<const V*>(a.R) + (long long)slot * a.H * a.n;
+  const double2* ph = a.phase + (size_t)(st.ik * 2) * 2 * kPhaseN;
   double v[3] = {0.0, 0.0, 0.0};
   for (long long u = threadIdx.x; u < np; u += blockDim.x) {
-    const double2 b = vload(r, (long long)planes[u / a.nxy] * a.nxy + u % a.nxy);
-    v[0] += b.x * b.x - b.y * b.y;
-    v[1] += 2.0 * b.x * b.y;
+    const long long pl = (long long)planes[u / a.nxy] * a.nxy;
+    const int w = (int)(u % a.nxy);
+    const double2 b = vload(r, pl + w);
+    double2 o = b;  // the pairing partner of b at this point
+    if (a.psym) {
+      const int y = w / a.nx, x = w - y * a.nx;
+      o = vload(r, pl + (x ? a.nx - x : 0) + (long long)a.nx * (y ? a.ny - y : 0));
+      if (x) o = cmul(o, ph[kPhaseW - 1]);
+      if (y) o = cmul(o, ph[kPhaseN + kPhaseW - 1]);
+    }
+    v[0] += o.x * b.x - o.y * b.y;
+    v[1] += o.x * b.y + o.y * b.x;
     v[2] += b.x * b.x + b.y * b.y;
   }
   block_sum<3>(v, red);
   if (threadIdx.x == 0) {
-    st.rho = make_double2(2.0 * v[0], 2.0 * v[1]);
+    const double f = a.psym ? 1.0 : 2.0;
+    st.rho = make_double2(f * v[0], f * v[1]);
     m.bnorm = sqrt(v[2]);
     a.escale[slot] = unit_exponent(m.bnorm);
   }
@@ -399,7 +418,7 @@ __global__ void __launch_bounds__(256) k_ms_coef(const MsArgs a) {
 }
 
 // p_sigma = r_n / pi_n + beta_sigma p_sigma, x_sigma += alpha_sigma p_sigma on the kept
-// planes, both halves, active shifts.  grid (ceil(no / 256), ne, S)
+// planes, every half, active shifts.  grid (ceil(no / 256), ne, S)
 __global__ void __launch_bounds__(256) k_ms_shift(const MsArgs a) {
   const int slot = blockIdx.z, s = blockIdx.y;
   if (a.slots[slot].status != SLOT_ACTIVE) return;
@@ -414,7 +433,8 @@ __global__ void __launch_bounds__(256) k_ms_shift(const MsArgs a) {
   const long long pt = (long long)planes[u / a.nxy] * a.nxy + u % a.nxy;
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const double2 rv = a.R[(long long)slot * 2 * a.n + (long long)h * a.n + pt];
+    if (h >= a.H) break;
+    const double2 rv = a.R[(long long)slot * a.H * a.n + (long long)h * a.n + pt];
     const long long off = (zs * 2 + h) * a.no + u;
     double2 pv = a.PS[off];
     pv = cadd(cmul(rv, co.inv_pi), cmul(co.beta_s, pv));
@@ -442,7 +462,8 @@ __global__ void __launch_bounds__(256) k_ms_shift_df(const MsArgs a) {
   float4* XS = reinterpret_cast<float4*>(a.XS);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
-    const dfc rv = dfc_load(R[(long long)slot * 2 * a.n + (long long)h * a.n + pt]);
+    if (h >= a.H) break;
+    const dfc rv = dfc_load(R[(long long)slot * a.H * a.n + (long long)h * a.n + pt]);
     const long long off = (zs * 2 + h) * a.no + u;
     const dfc pv = dfc_add(dfc_mul(rv, inv_pi), dfc_mul(beta_s, dfc_load(PS[off])));
     PS[off] = dfc_store(pv);
@@ -589,6 +610,28 @@ __global__ void k_ms_release(const MsArgs a) {
   a.queue->harvested += h;
 }
 
+// P-symmetric runs iterate the primal half alone.  Their shadow half of the kept planes
+// is filled with P_k x: by A(-k) P_k = P_k A(k) (V invariant under the in-plane
+// inversion R_{z,pi}, Sec. II.C), P_k x solves A(-k) y = P_k b, so it is the shadow
+// solution for the mirrored right-hand side P_k b.  grid (ceil(no / 256), ne, S)
+template <typename V>
+__global__ void __launch_bounds__(256) k_ms_psym_fill(const MsArgs a) {
+  const int slot = blockIdx.z, s = blockIdx.y;
+  const long long zs = (long long)slot * a.ne + s;
+  const long long nro = (long long)(a.ms[slot].kind == RUN_RIGHT ? a.nlp : a.nrp) * a.nxy;
+  const long long u = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= nro) return;
+  const double2* ph = a.phase + (size_t)(a.slots[slot].ik * 2) * 2 * kPhaseN;
+  const long long pl = u / a.nxy;
+  const int w = (int)(u - pl * a.nxy);
+  const int y = w / a.nx, x = w - y * a.nx;
+  V* xs = reinterpret_cast<V*>(a.XS);
+  double2 o = vload(xs, zs * 2 * a.no + pl * a.nxy + (x ? a.nx - x : 0) + (long long)a.nx * (y ? a.ny - y : 0));
+  if (x) o = cmul(o, ph[kPhaseW - 1]);
+  if (y) o = cmul(o, ph[kPhaseN + kPhaseW - 1]);
+  vstore(xs, (zs * 2 + 1) * a.no + u, o);
+}
+
 // ---------------------------------------------------------------------------------
 // two-sided sketch reduction: T(E, +-k) per shift from the LEFT / RIGHT runs
 // ---------------------------------------------------------------------------------
@@ -611,6 +654,10 @@ struct GnArgs {
   int* rank;               // [rep][ne][2]
   int* status;             // [rep][ne][2]
   double drop;             // relative norm below which a column of Y adds no direction
+  int psym;                // P-symmetric runs: the +k rows of W belong to P_k psi
+  int nx, ny;
+  const Slot* slots;
+  const double2* phase;    // [nk][2][2][kPhaseN] Bloch phases
 };
 
 constexpr int kGnMaxL = 32, kGnMaxR = 64;
@@ -735,8 +782,12 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
     if (threadIdx.x == 0) s_keep[c] = keep;
     __syncthreads();
   }
-  // K[i][c] = psi_i^T q_c (bilinear) for the kept columns
+  // K[i][c] = psi_i^T q_c (bilinear) for the kept columns.  With P-symmetric runs the
+  // +k rows of W came from P_k x of the RIGHT runs, so they belong to the test vectors
+  // P_k psi_i
   const double2* psi = a.rnd + ((long long)rep * 2 + 1) * a.smax * a.np;
+  const bool mirror = a.psym && sign == 0;
+  const double2* ph = a.phase + (size_t)(a.slots[rs[0]].ik * 2) * 2 * kPhaseN;
   for (int i = 0; i < sr; ++i) {
     const double2* pv = psi + (long long)i * a.np;
     for (int j0 = 0; j0 < sl; j0 += kGnChunk) {
@@ -744,7 +795,15 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
 #pragma unroll
       for (int k = 0; k < 2 * kGnChunk; ++k) v[k] = 0.0;
       for (long long u = threadIdx.x; u < nR; u += blockDim.x) {
-        const double2 p = pv[u];
+        double2 p = pv[u];
+        if (mirror) {
+          const long long pl = u / a.nxy;
+          const int w = (int)(u - pl * a.nxy);
+          const int y = w / a.nx, x = w - y * a.nx;
+          p = pv[pl * a.nxy + (x ? a.nx - x : 0) + (long long)a.nx * (y ? a.ny - y : 0)];
+          if (x) p = cmul(p, ph[kPhaseW - 1]);
+          if (y) p = cmul(p, ph[kPhaseN + kPhaseW - 1]);
+        }
 #pragma unroll
         for (int k = 0; k < kGnChunk; ++k) {
           const int j = j0 + k;
@@ -981,12 +1040,14 @@ cudaError_t grow(P*& p, size_t have, size_t need) {
 
 // One solve of the multi-shift engine: items run to completion (every shift converged
 // or stopped), per-shift vectors left in the buffers for the reductions.
+// psym: P-symmetric COCG (one half per run; double-float form, the plane in one tile).
 int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vector<double>& energies,
               double e0, int S, int nrep, int smax, unsigned long long seed, double** d_res_t,
-              int** d_res_it, int** d_res_st) {
+              int** d_res_it, int** d_res_st, bool psym = false) {
   SweepBufs& B = *ctx->sweep;
   const Geometry& g = ctx->g;
   const bool dfm = ctx->opts.precision == TRANSEC_PREC_DF64;  // double-float kernels
+  const int H = psym ? 1 : 2;
   const int ne = (int)energies.size();
   const int nitems = (int)items.size();
   const long long n = g.n, nxy = g.nxy;
@@ -995,8 +1056,10 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   // the double-float stencil spends a larger share on the 2R-plane prologue of a slab,
   // so its default slab is deeper
   const int slab = ctx->opts.slab > 0 ? ctx->opts.slab : (dfm ? 64 : 0);
-  const TileShape ts = choose_tiles(g, 2, sizeof(double2), dfm ? kDfThreads : StencilMax<double>::threads,
+  const TileShape ts = choose_tiles(g, H, sizeof(double2), dfm ? kDfThreads : StencilMax<double>::threads,
                                     ctx->opts.tile_y, slab);
+  if (psym && (!dfm || ts.ntx != 1 || ts.nty != 1 || ts.TX != g.nx || ts.TY != g.ny))
+    return ms_fail(ctx, TRANSEC_EINVAL, "P-symmetric runs need the double-float form and a plane in one tile");
   const int nblk_st = ts.ntx * ts.nty * ts.nslab;
   // blocks per run of the vector update: the double-float update sets up its scalars
   // in FP64 once per thread, so it takes more points per thread (about 8 blocks per SM
@@ -1085,9 +1148,10 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   a.rho_part = B.rho_part; a.nblk3 = nblk3; a.sig_part = B.sig_part; a.nblk_st = nblk_st;
   a.tol = ctx->opts.tol; a.maxit = ctx->opts.maxit; a.escale = B.escale;
   a.stall_its = dfm ? ctx->opts.df_stall_its : 0;
+  a.H = H; a.psym = psym ? 1 : 0; a.nx = g.nx; a.ny = g.ny; a.phase = ctx->d_phase;
   a.res_t = res_t; a.res_it = res_it; a.res_st = res_st;
 
-  const size_t smem_df = stencil_df_smem(g.R, ts.TX, ts.TY, 2, ts.threads);
+  const size_t smem_df = stencil_df_smem(g.R, ts.TX, ts.TY, H, ts.threads);
   bool iso = true;
   for (int m = 1; m <= g.R; ++m) iso = iso && g.kx[m] == g.ky[m] && g.kx[m] == g.kz[m];
   if (dfm) MS_CK(stencil_df(g.R, iso, dim3(1), 0, smem_df, st, StencilDfArgs{}, true));
@@ -1101,12 +1165,17 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
     da.ky[m] = make_float2(y.hi, y.lo);
     da.kz[m] = make_float2(z.hi, z.lo);
   }
-  da.diag_c = g.diag_c; da.nx = g.nx; da.ny = g.ny; da.nz = g.nz; da.nxy = g.nxy; da.n = g.n; da.H = 2;
-  da.TX = ts.TX; da.TY = ts.TY; da.D = ts.D; da.ntx = ts.ntx; da.conj = 0; da.slot_stride = 2 * n;
+  da.diag_c = g.diag_c; da.nx = g.nx; da.ny = g.ny; da.nz = g.nz; da.nxy = g.nxy; da.n = g.n; da.H = H;
+  da.TX = ts.TX; da.TY = ts.TY; da.D = ts.D; da.ntx = ts.ntx; da.conj = 0; da.slot_stride = H * n;
+  da.psym = psym ? 1 : 0;
   UpdateDfArgs dua{};
   dua.r = reinterpret_cast<float4*>(B.R); dua.q = reinterpret_cast<const float4*>(B.Q); dua.sig_part = B.sig_part;
   dua.sig_nblk = nblk_st; dua.rho_part = B.rho_part; dua.slots = B.slots; dua.escale = B.escale; dua.n = n;
   dua.slot_stride = 2 * n; dua.H = 2;
+  UpdateDfPsymArgs dpa{};
+  dpa.r = dua.r; dpa.q = dua.q; dpa.sig_part = B.sig_part; dpa.sig_nblk = nblk_st; dpa.rho_part = B.rho_part;
+  dpa.slots = B.slots; dpa.escale = B.escale; dpa.phase = B.phase_df; dpa.nx = g.nx; dpa.ny = g.ny;
+  dpa.nxy = nxy; dpa.n = n; dpa.slot_stride = n;
   StencilArgs<double> sa{};
   sa.r = B.R; sa.q = B.Q; sa.part = B.sig_part; sa.slots = B.slots; sa.phase = ctx->d_phase;
   sa.v = ctx->d_v; sa.gam = ctx->d_gam; sa.g = g; sa.H = 2; sa.TX = ts.TX; sa.TY = ts.TY; sa.D = ts.D;
@@ -1183,7 +1252,8 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
     else k_ms_shift<<<shgrid, 256, 0, st>>>(a);
     if (prof) cudaEventRecordWithFlags(ctx->prof_ev[4 * i + 3], st, cudaEventRecordExternal);
     ua.p = sa.p_out;
-    if (dfm) k_update_df<<<ugrid, 256, 0, st>>>(dua);
+    if (psym) k_update_df_psym<<<ugrid, 256, 0, st>>>(dpa);
+    else if (dfm) k_update_df<<<ugrid, 256, 0, st>>>(dua);
     else k_update<double><<<ugrid, 256, 0, st>>>(ua);
     k_ms_scalars<<<S, 256, 0, st>>>(a);
   }
@@ -1278,7 +1348,7 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
         int mx = 0;
         for (int e = 0; e < ne; ++e) {
           mx = std::max(mx, hsh[(size_t)s2 * ne + e].conv_it);
-          ctx->sweep_shift_points += (long long)hsh[(size_t)s2 * ne + e].conv_it * 2 * (long long)std::max(nlp, nrp) * nxy;
+          ctx->sweep_shift_points += (long long)hsh[(size_t)s2 * ne + e].conv_it * H * (long long)std::max(nlp, nrp) * nxy;
         }
         ctx->sweep_iters += mx;
       }
@@ -1354,9 +1424,9 @@ int columns_solve(transec_ctx* ctx, const std::vector<double>& es, const std::ve
 }
 
 // Full trace T(E, k), T(E, -k) of the k groups ik by the two-sided sketch, in the
-// context's precision.  Outputs [group][energy].
+// context's precision (psym: P-symmetric COCG runs).  Outputs [group][energy].
 int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vector<int>& ik, int s_left,
-                 int s_right, unsigned long long seed, SweepOut& out) {
+                 int s_right, unsigned long long seed, SweepOut& out, bool psym = false) {
   const int ne = (int)es.size(), nrep = (int)ik.size();
   const int per = s_left + s_right;
   std::vector<MsItem> items;
@@ -1376,7 +1446,8 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
   if (!ctx->sweep) ctx->sweep = new SweepBufs();
   double* rt = nullptr;
   int *rit = nullptr, *rst = nullptr;
-  int rc = run_sweep(ctx, items, es, seed_energy(es), S, nrep, std::max(s_left, s_right), seed, &rt, &rit, &rst);
+  int rc = run_sweep(ctx, items, es, seed_energy(es), S, nrep, std::max(s_left, s_right), seed, &rt, &rit, &rst,
+                     psym);
   cudaFree(rt);
   cudaFree(rit);
   cudaFree(rst);
@@ -1403,6 +1474,16 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
     cudaEventCreate(&g1);
     cudaEventRecord(g0, ctx->s);
   }
+  if (e == cudaSuccess && psym) {
+    MsArgs fa{};
+    fa.slots = B.slots; fa.ms = B.ms; fa.XS = B.XS; fa.ne = ne; fa.no = B.no; fa.nxy = ctx->g.nxy;
+    fa.nlp = (int)ctx->lplanes.size(); fa.nrp = (int)ctx->rplanes.size(); fa.nx = ctx->g.nx; fa.ny = ctx->g.ny;
+    fa.phase = ctx->d_phase;
+    const dim3 fgrid((unsigned)((B.no + 255) / 256), (unsigned)ne, (unsigned)S);
+    k_ms_psym_fill<float4><<<fgrid, 256, 0, ctx->s>>>(fa);
+    ctx->launches += 1;
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) {
     GnArgs ga{};
     ga.XS = B.XS; ga.sh = B.sh; ga.run_slot = d_rs; ga.rnd = B.rnd; ga.smax = std::max(s_left, s_right);
@@ -1410,6 +1491,7 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
     ga.lplanes = ctx->d_lplanes; ga.rplanes = ctx->d_rplanes; ga.nlp = (int)ctx->lplanes.size();
     ga.nrp = (int)ctx->rplanes.size(); ga.gl = ctx->d_gl; ga.gr = ctx->d_gr; ga.T = d_T; ga.rank = d_rank;
     ga.status = d_st; ga.drop = 1e-13;
+    ga.psym = psym ? 1 : 0; ga.nx = ctx->g.nx; ga.ny = ctx->g.ny; ga.slots = B.slots; ga.phase = ctx->d_phase;
     if (dfm) k_ms_gn<float4><<<dim3((unsigned)ne, (unsigned)nrep, 2), 256, smem, ctx->s>>>(ga);
     else k_ms_gn<double2><<<dim3((unsigned)ne, (unsigned)nrep, 2), 256, smem, ctx->s>>>(ga);
     ctx->launches += 1;
@@ -1575,12 +1657,20 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
   for (int r = 0; r < nrep; ++r)
     if (ik[r] < 0 || ik[r] >= ctx->nk) return ms_fail(ctx, TRANSEC_EINVAL, "k index out of range");
   if (ctx->rplanes.empty()) return ms_fail(ctx, TRANSEC_EINVAL, "right absorbing profile is zero everywhere");
+  const bool psym = ctx->opts.psym != 0;
+  if (psym) {
+    if (ctx->opts.precision != TRANSEC_PREC_DF64)
+      return ms_fail(ctx, TRANSEC_EINVAL, "P-symmetric runs are built in the double-float form (precision 2)");
+    if (!(ctx->v_inversion_gap <= kPsymTol))
+      return ms_fail(ctx, TRANSEC_EINVAL, "the potential is not invariant under the in-plane inversion about grid "
+                                          "point (0, 0)");
+  }
   DevScope ds(ctx->device);
   MS_CK(cudaStreamSynchronize(ctx->user));
   const std::vector<double> es(energies, energies + ne);
   const std::vector<int> hik(ik, ik + nrep);
   SweepOut out;
-  int rc = sketch_solve(ctx, es, hik, s_left, s_right, seed, out);
+  int rc = sketch_solve(ctx, es, hik, s_left, s_right, seed, out, psym);
   if (rc != TRANSEC_OK) return rc;
   // double-float results that did not converge: the failed k groups again with FP64
   // runs at the energies that failed for any of them (a fresh random draw)

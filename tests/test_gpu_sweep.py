@@ -7,7 +7,8 @@
   same numbers as runs that all fit at once.
 * transec_transmission_sketch: the full trace T(E, k) = 4 Tr[Gamma_L G^dagger Gamma_R G]
   from random left and right right-hand sides, against the dense-LU full trace over
-  every left-CAP column, at k and -k, within |dT| <= 1e-6 (the metric's bar).
+  every left-CAP column, at k and -k, within |dT| <= 1e-6 (the metric's bar); also
+  with P-symmetric COCG runs on inversion-symmetric cells (Sec. II.C).
 
 Both arithmetics of the engine are covered: FP64 (precision 0) and double-float
 (precision 2: vectors and the stencil, vector and per-shift updates in pairs of floats).
@@ -17,7 +18,9 @@ import numpy as np
 import pytest
 
 from tests.gpu_util import context, library, need_gpu
-from workloads import small_instance
+import dataclasses
+
+from workloads import inversion_symmetrize, small_instance
 from oracle.transmission import left_support, transmission_dense
 
 pytestmark = pytest.mark.gpu
@@ -179,3 +182,58 @@ def test_double_float_results_that_stall_are_solved_again_in_fp64():
     assert redone_all - redone_cols == energies.size
     assert np.all(sk["status"] == 0)
     assert np.abs(sk["T"] - sk_ref["T"]).max() <= TOL_T
+
+
+def _sym_inst(kf, nx, ny, nz, order, seed):
+    inst = small_instance(nx, ny, nz, 0.45, order, 9, v_amp=0.7, kfrac=(kf, (-kf[0], -kf[1])),
+                          energies=(0.3,), seed=seed)
+    return dataclasses.replace(inst, v=inversion_symmetrize(inst.v))
+
+
+@pytest.mark.parametrize("kf,order,shape", [((0.23, -0.37), 8, (6, 6, 44)), ((0.4375, 0.3125), 12, (5, 4, 40)),
+                                            ((0.0, 0.0), 4, (7, 6, 40))])
+def test_psym_sketch_matches_dense_lu(kf, order, shape):
+    """P-symmetric COCG runs (one operator application per iteration) on cells whose V
+    is invariant under the in-plane inversion: T(E, k) and T(E, -k) against the dense-LU
+    full trace; the -k estimate is the mirrored data, equal to T to rounding; the runs
+    update one half (half the per-shift points of transpose BiCG)."""
+    need_gpu()
+    inst = _sym_inst(kf, *shape, order, seed=17)
+    g = inst.grid
+    energies = np.linspace(0.1, 0.9, 7)
+    with context(inst, precision=2, psym=1) as tr:
+        tr.stats_reset()
+        r = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=3)
+        ps = tr.sweep_stats()
+        tr.set_solver(psym=0)
+        tr.stats_reset()
+        b = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=3)
+        bs = tr.sweep_stats()
+    assert np.all(r["status"] == 0) and np.all(b["status"] == 0), (r["status"], b["status"])
+    assert ps["fp64_redone"] == 0
+    for s, e in enumerate(energies):
+        tp, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf)
+        tm, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, (-kf[0], -kf[1]))
+        assert abs(r["T"][0, s] - tp) <= TOL_T, (e, r["T"][0, s], tp)
+        assert abs(r["T_minus"][0, s] - tm) <= TOL_T, (e, r["T_minus"][0, s], tm)
+        assert abs(r["T"][0, s] - b["T"][0, s]) <= TOL_T
+        assert 1 <= r["rank"][0, s] <= 8
+    assert np.abs(r["T"] - r["T_minus"]).max() <= 1e-9
+    # per-shift work: one half per iteration against two
+    per_it_p = ps["shift_points"] / max(1, ps["iters"])
+    per_it_b = bs["shift_points"] / max(1, bs["iters"])
+    assert per_it_p < 0.75 * per_it_b, (per_it_p, per_it_b)
+
+
+def test_psym_argument_checks():
+    need_gpu()
+    pkg = library()
+    kf = (0.23, -0.37)
+    sym = _sym_inst(kf, 6, 6, 40, 8, seed=17)
+    asym = _inst(kf)
+    wide = _sym_inst(kf, 30, 30, 30, 4, seed=2)  # 900 points: the plane does not fit one tile
+    for inst, prec in ((sym, 0), (asym, 2), (wide, 2)):
+        with context(inst, precision=prec, psym=1) as tr:
+            with pytest.raises(pkg.TransecError) as ei:
+                tr.transmission_sketch([0.3], [0], s_left=4, s_right=8)
+            assert ei.value.status == pkg.EINVAL

@@ -18,6 +18,8 @@ from .configs import (  # noqa: F401
     sommerfeld_fermi,
     free_electron_slab,
     cu_bulk,
+    cu_bulk_ideal,
+    inversion_symmetrize,
     rh_point_contact,
     uneven_batch,
     small_instance,

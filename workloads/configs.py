@@ -18,6 +18,7 @@ Seeds follow ``seed = 1000*config + instance``.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+import dataclasses
 import math
 
 import numpy as np
@@ -301,6 +302,26 @@ def cu_bulk(instance: int = 0) -> Instance:
         "bulk fcc Cu [001] 20x20x480 order 12", 6.82, 1, 1, 20, 20, 480, 12, 1.2, 0.9,
         0.02, 64, 0.3, (8, 8), 256, 0.3, config_seed(2, instance),
     )
+
+
+def inversion_symmetrize(v: np.ndarray) -> np.ndarray:
+    """(V + V o R_{z,pi}) / 2 for an (nz, ny, nx) array, R_{z,pi} the in-plane inversion
+    (x, y) -> (-x mod nx, -y mod ny) about grid point (0, 0): the result is invariant
+    under it to the last bit (a + b = b + a)."""
+    vm = np.roll(v[:, ::-1, ::-1], shift=(1, 1), axis=(1, 2))
+    return 0.5 * (v + vm)
+
+
+def cu_bulk_ideal(instance: int = 0) -> Instance:
+    """The bulk Cu cell of ``cu_bulk`` without the amplitude jitter: the ideal fcc
+    crystal, whose in-plane inversion about an atom (grid point (0, 0)) is a symmetry
+    (the C2 rotation about z of Sec. II.C).  V is symmetrised so that the invariance
+    holds to the last bit (the lattice sums leave rounding-level asymmetry)."""
+    inst = _crystal(
+        "ideal bulk fcc Cu [001] 20x20x480 order 12", 6.82, 1, 1, 20, 20, 480, 12, 1.2, 0.9,
+        0.0, 64, 0.3, (8, 8), 256, 0.3, config_seed(2, instance),
+    )
+    return dataclasses.replace(inst, v=inversion_symmetrize(inst.v))
 
 
 def rh_point_contact(instance: int = 0) -> Instance:
