@@ -175,7 +175,7 @@ def _oracle_worker(args):
     on one seeded column of the workload for a bounded number of iterations; returns
     the seconds per iteration.  The workload's operator is built once per process."""
     workload, e, kf, col, budget_s = args
-    from workloads import cu_bulk, rh_point_contact
+    from workloads import cu_bulk, rh_point_contact, uneven_batch
     from oracle.hamiltonian import system_matrix
     from oracle.transmission import bicg_transpose, left_support
 
@@ -183,7 +183,10 @@ def _oracle_worker(args):
     if key not in _ORACLE_CACHE:
         inst = _ORACLE_CACHE.get(workload)
         if inst is None:
-            inst = rh_point_contact() if workload == "rh_point_contact" else cu_bulk()
+            if workload.startswith("uneven_batch:"):
+                inst = uneven_batch(96, only=[int(workload.split(":")[1])])[0]
+            else:
+                inst = rh_point_contact() if workload == "rh_point_contact" else cu_bulk()
             _ORACLE_CACHE[workload] = inst
         g = inst.grid
         _ORACLE_CACHE.clear()
@@ -305,9 +308,11 @@ def run_reference(args):
 def run_uneven_batch(args):
     """Configuration 4: 96 seeded Cu/Rh bulk and point-contact cells of uneven size.
     A step takes one seeded (E at mid-window, k, column) item from each of 16 seeded
-    cells and solves them together in one batched launch (one slot engine, the cells'
-    operators in a table); the same items solved one cell at a time give the looped
-    figure.  Reports column-solves/s of both and their ratio."""
+    cells and solves them together in one batched call (one slot engine, the cells'
+    operators in a table) in the mixed FP32/FP64 form (``--form fp64``: plain FP64),
+    with the tile height, slab depth and slots chosen by transec_autotune on the driver
+    context; the same items solved one cell at a time in plain FP64 give the looped
+    time-to-T figure.  Reports column-solves/s of both and their ratio."""
     import torch
 
     from workloads import uneven_batch
@@ -315,10 +320,11 @@ def run_uneven_batch(args):
     from paper_2208_02783_gb300 import build
 
     pkg.load(build.build())
-    prec = pkg.PREC_MIXED if args.form == "mixed" else pkg.PREC_FP64
+    prec = pkg.PREC_FP64 if args.form == "fp64" else pkg.PREC_MIXED
     insts = uneven_batch(96)
     ctxs = [pkg.Transec.from_instance(i, device=0, tol=1e-10, precision=prec) for i in insts]
     per_step = 16
+    tuned = ctxs[0].autotune(float(insts[0].energies[len(insts[0].energies) // 2]), 0)
 
     def items(step):
         rng = np.random.default_rng(4000 + step)
@@ -328,10 +334,15 @@ def run_uneven_batch(args):
         col = np.array([rng.integers(0, insts[c].n_rhs) for c in cells], np.int64)
         return cells.astype(np.int32), e, k, col
 
+    def set_all(**kw):
+        for c in ctxs:
+            c.set_solver(**kw)
+
     for s in range(args.warmup):
         cells, e, k, col = items(s)
         pkg.batch_column_contributions(ctxs, cells, e, k, col)
     torch.cuda.synchronize()
+    ctxs[0].stats_reset()
     t_batch = 0.0
     t_loop = 0.0
     its = 0
@@ -339,36 +350,103 @@ def run_uneven_batch(args):
     dt_max = 0.0
     rel_max = 0.0
     statuses = []
+    its_items = []
+    clocks = Clocks(0)
+    clocks.start()
     for s in range(args.steps):
         cells, e, k, col = items(args.warmup + s)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         r = pkg.batch_column_contributions(ctxs, cells, e, k, col)
         t_batch += time.perf_counter() - t0
         its += int(r["iters"].sum())
         fails += int((r["status"] != 0).sum())
+        set_all(precision=pkg.PREC_FP64)
         t0 = time.perf_counter()
         for u, c in enumerate(cells):
             q = ctxs[c].column_contributions(e[u:u + 1], k[u:u + 1], col[u:u + 1])
             statuses.append((int(r["status"][u]), int(q["status"][0])))
+            its_items.append((int(c), float(e[u]), int(k[u]), int(col[u]), int(q["iters"][0])))
             d = abs(q["t"][0] - r["t"][u])
             dt_max = max(dt_max, d)
             rel_max = max(rel_max, d / max(abs(q["t"][0]), 1e-300))
         t_loop += time.perf_counter() - t0
+        set_all(precision=prec)
+    clk = clocks.stop()
+    st = ctxs[0].stats()
     n = per_step * args.steps
+    value = n / t_batch
+
+    # profiled pass (separate): one step's items with the driver's stencil launches timed
+    cells, e, k, col = items(args.warmup + args.steps)
+    ctxs[0].set_solver(profile=1, maxit=400)
+    ctxs[0].stats_reset()
+    pkg.batch_column_contributions(ctxs, cells, e, k, col)
+    stp = ctxs[0].stats()
+    ctxs[0].set_solver(profile=0, maxit=100000)
+    peaks = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", HBM_FALLBACK_GBS))
+    order = insts[0].grid.order
+    if prec == pkg.PREC_FP64:
+        pa, sten_ms, nl = stp["point_applies"], stp["stencil_ms"], max(1, stp["stencil_launches"])
+        flops = pa * stencil_flops_per_point(order)
+        achieved = flops / (sten_ms / 1e3) / 1e12 if sten_ms > 0 else 0.0
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_stencil<double,6> (batched)",
+                "per_launch": {"flops": flops / nl, "ms": sten_ms / nl},
+                "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"}
+    else:
+        pa, sten_ms, nl = stp["point_applies32"], stp["stencil32_ms"], max(1, stp["stencil32_launches"])
+        byts = pa * stencil_bytes_per_point(8)
+        achieved = byts / (sten_ms / 1e3) / 1e9 if sten_ms > 0 else 0.0
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_stencil<float,6> (batched)",
+                "per_launch": {"bytes": byts / nl, "ms": sten_ms / nl},
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    roof["timing"] = ("separate profiled pass: one step's 16 items, at most 400 iterations, CUDA events "
+                      "around every stencil launch on the driver context's stream")
     line = {
-        "metric": "uneven batch column-solves/s (batched one launch vs looped per cell)",
-        "value": n / t_batch, "unit": "column-solves/s", "n_gpus": 1, "steps": args.steps,
+        "metric": "uneven batch column-solves/s (batched one call vs looped per cell in plain FP64)",
+        "value": value, "unit": "column-solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_batch / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128" if prec == pkg.PREC_FP64 else "c64+f64",
         "data": "synthetic",
         "config": {"workload": "96 seeded Cu/Rh bulk and point-contact cells, 1x1-4x4 cells wide, "
                                "12-40 cells long, h 0.30-0.40, order 12 (configuration 4)",
-                   "items_per_step": per_step, "looped_column_solves_per_s": n / t_loop,
-                   "batched_over_looped": t_loop / t_batch, "mean_iterations": its / n,
-                   "failed_batched": fails, "max_abs_dt_batched_vs_looped": dt_max,
-                   "max_rel_dt_batched_vs_looped": rel_max,
-                   "statuses_batched_looped": sorted(set(statuses))},
+                   "form": ("plain FP64 transpose BiCG" if prec == pkg.PREC_FP64 else
+                            "mixed: complex FP32 BiCG with FP64 scalars and residual replacement, FP64 fallback"),
+                   "autotuned": tuned,
+                   "items_per_step": per_step, "looped_fp64_column_solves_per_s": n / t_loop,
+                   "batched_over_looped": t_loop / t_batch, "mean_iterations_batched": its / n,
+                   "fp64_fallback_columns": int(st.get("fallbacks", 0)),
+                   "failed_batched": fails, "max_abs_dt_batched_vs_looped_fp64": dt_max,
+                   "max_rel_dt_batched_vs_looped_fp64": rel_max,
+                   "statuses_batched_looped": sorted(set(statuses)),
+                   "timing": "host wall clock around each call (host arrays in and out)"},
+        "roofline": roof,
+        "e2e": {"value": value, "unit": "column-solves/s", "h2d_bytes_per_step": per_step * (8 + 4 + 8 + 4),
+                "d2h_bytes_per_step": per_step * (8 + 8 + 4 + 4),
+                "note": "the timed value is already end to end: the public call with host arrays"},
+        "gpu_launches": int(st["launches"]),
+        "clocks": clk,
     }
+    if not args.no_cpu_baseline:
+        # the oracle on the host cores: each process runs the oracle's transpose BiCG on
+        # one timed item's cell and column; its column time is its time per iteration x
+        # the FP64 iterations the looped GPU solve of that column took
+        sample = its_items[:min(len(its_items), os.cpu_count() or 1, 16)]
+        with OraclePool("cu_bulk", procs=len(sample)) as op:
+            jobs = [(f"uneven_batch:{c}", e_, tuple(map(float, insts[c].kfrac[k_])), col_, 6.0)
+                    for c, e_, k_, col_, _ in sample]
+            res = op.pool.map(_oracle_worker, jobs, chunksize=1)
+        crate = sum(1.0 / (per_it * max(1, it_)) for (per_it, _, _), (*_, it_) in zip(res, sample))
+        line["cpu_baseline"] = {
+            "value": crate, "unit": "column-solves/s", "cores": len(sample), "kind": "oracle",
+            "sample": (f"oracle transpose BiCG (numpy/scipy complex128), one single-threaded process per core "
+                       f"({len(sample)}), each on the cell and column of one timed item for a bounded number of "
+                       "iterations (about 2 s); column time = time per iteration x the FP64 iterations of that "
+                       "column on the GPU; rates summed"),
+        }
     print(json.dumps(line))
     for c in ctxs:
         c.close()
@@ -737,6 +815,24 @@ def run_learned(args):
         "gpu_launches": 18 * steps,
         "clocks": clk,
     }
+    if not args.no_cpu_baseline:
+        # the oracle's forward (NumPy, float64 with the same BF16 rounding points) on a
+        # bounded slab of the volume, 20 x 20 x 16 voxels, on one host core
+        from oracle import unet as ref
+
+        p = ref.init_params(1)
+        xs = np.random.default_rng(0).normal(size=(16, 20, 20, 4))
+        ref.forward(p, xs, bf16=True)
+        t0 = time.perf_counter()
+        reps_cpu = 0
+        while time.perf_counter() - t0 < 10.0:
+            ref.forward(p, xs, bf16=True)
+            reps_cpu += 1
+        dt = (time.perf_counter() - t0) / reps_cpu
+        line["cpu_baseline"] = {"value": xs[..., 0].size / dt, "unit": "voxels/s", "cores": 1, "kind": "oracle",
+                                "sample": f"oracle.unet.forward on a 20x20x16 slab, {reps_cpu} forwards in "
+                                          f"{dt * reps_cpu:.1f} s (NumPy; its BLAS kept to one thread by the "
+                                          "environment when OMP_NUM_THREADS=1)"}
     print(json.dumps(line))
     return 0
 

@@ -115,6 +115,12 @@ typedef struct transec_solver_opts {
                          precision = TRANSEC_PREC_DF64, a potential that passes the
                          inversion check of transec_set_potential, nx <= 32 and
                          nx * ny <= 896; other entry points ignore it.  Default 0 */
+  double sketch_guard; /* transec_transmission_sketch with transpose-BiCG runs: a result
+                         whose two independent estimates differ by more,
+                         |T(E, k) - T(E, -k)| > sketch_guard, is computed again with a
+                         sketch of twice the sizes (up to 32 + 64) and a fresh draw, up to
+                         three times; default 1e-7 (a tenth of the 1e-6 bar on T),
+                         negative = never */
 } transec_solver_opts;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -413,7 +419,10 @@ int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, in
  * mirrored, so T_minus equals T to rounding and is no independent estimate; EINVAL
  * when opts.psym is set with another precision, a potential that is not
  * inversion-symmetric (relative gap above 1e-12) or a plane too large for one tile.
- * The FP64 re-solve of failed results uses transpose BiCG.  Host arrays.
+ * The FP64 re-solve of failed results uses transpose BiCG.  Without opts.psym, results
+ * whose T and T_minus differ by more than opts.sketch_guard are computed again with a
+ * doubled sketch (the a-posteriori check acting); rank_out then reports the larger
+ * sketch's rank and iters_out adds its iterations.  Host arrays.
  * Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT; per-result ENOCONV / EBREAKDOWN with
  * T = NaN.
  */
@@ -429,13 +438,14 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
  * shifted-update kernels (ms, launches) of the FP64 runs and, apart, of the
  * double-float runs (the *_df outputs), and the sketch reduction (ms), and the
  * (energy, column or k) results of double-float calls that were solved again in FP64
- * (fp64_redone).  Any output may be NULL.
+ * (fp64_redone), and the (energy, k) results of sketch calls computed again with a
+ * larger sketch under opts.sketch_guard (guard_redone).  Any output may be NULL.
  */
 int transec_sweep_stats(const transec_ctx* ctx, long long* iters, long long* shift_points,
                         double* stencil_ms, long long* stencil_launches, double* shift_ms,
                         long long* shift_launches, double* stencil_df_ms, long long* stencil_df_launches,
                         double* shift_df_ms, long long* shift_df_launches, double* reduce_ms,
-                        long long* fp64_redone);
+                        long long* fp64_redone, long long* guard_redone);
 
 /* Message of the last failure on this context ("" if none).  Valid until the next
  * call on the same context. */

@@ -51,6 +51,7 @@ class SolverOpts(C.Structure):
         ("host_loop", C.c_int),
         ("df_stall_its", C.c_int),
         ("psym", C.c_int),
+        ("sketch_guard", C.c_double),
     ]
 
 
@@ -105,7 +106,7 @@ _SIGS = {
                                       C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                       C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
-                                      C.POINTER(C.c_longlong)]),
+                                      C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "transec_unet_destroy": (None, [_P]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
@@ -533,9 +534,10 @@ def transec_transmission_sketch(ctx, energies, ik, s_left=16, s_right=32, seed=0
 
 def transec_sweep_stats(ctx) -> dict:
     v = [C.c_longlong(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(),
-         C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong()]
+         C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(),
+         C.c_longlong()]
     _check(ctx, load().transec_sweep_stats(ctx, *[C.byref(x) for x in v]), "transec_sweep_stats")
     keys = ("iters", "shift_points", "stencil_ms", "stencil_launches", "shift_ms", "shift_launches",
             "stencil_df_ms", "stencil_df_launches", "shift_df_ms", "shift_df_launches", "reduce_ms",
-            "fp64_redone")
+            "fp64_redone", "guard_redone")
     return {k: x.value for k, x in zip(keys, v)}

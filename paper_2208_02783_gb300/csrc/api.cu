@@ -96,6 +96,7 @@ void default_opts(transec_solver_opts* o) {
   if (o->mixed_maxit <= 0) o->mixed_maxit = 8000;
   if (o->mixed_decade_its == 0) o->mixed_decade_its = 1000;
   if (o->df_stall_its == 0) o->df_stall_its = 8000;
+  if (o->sketch_guard == 0) o->sketch_guard = 1e-7;
 }
 
 // Bloch phase exp(2 pi i kappa w) with the argument reduced before the cosine.
@@ -1024,7 +1025,7 @@ int transec_set_solver(transec_ctx* ctx, const transec_solver_opts* opts) {
   transec_solver_opts o = *opts;
   if (o.method < 0 || o.method > 2 || o.precision < 0 || o.precision > 2 || o.tol < 0 ||
       o.maxit < 0 || o.slots < 0 || o.chunk < 0 || o.tile_y < 0 || o.slab < 0 || o.mixed_maxit < 0 ||
-      o.psym < 0 || o.psym > 1 ||
+      o.psym < 0 || o.psym > 1 || !std::isfinite(o.sketch_guard) ||
       !std::isfinite(o.tol) || !std::isfinite(o.reliable))
     return fail(ctx, TRANSEC_EINVAL, "invalid solver options");
   default_opts(&o);
@@ -1468,6 +1469,7 @@ int transec_stats_reset(transec_ctx* ctx) {
   ctx->sweep_stencil_ms = ctx->sweep_shift_ms = ctx->sweep_update_ms = ctx->sweep_reduce_ms = 0;
   ctx->sweep_stencil_launches = ctx->sweep_shift_launches = 0;
   ctx->sweep_fp64_redone = 0;
+  ctx->sweep_guard_redone = 0;
   ctx->sweep_stencil_df_ms = ctx->sweep_shift_df_ms = 0;
   ctx->sweep_stencil_df_launches = ctx->sweep_shift_df_launches = 0;
   return TRANSEC_OK;
@@ -1477,8 +1479,9 @@ int transec_sweep_stats(const transec_ctx* ctx, long long* iters, long long* shi
                         double* stencil_ms, long long* stencil_launches, double* shift_ms,
                         long long* shift_launches, double* stencil_df_ms, long long* stencil_df_launches,
                         double* shift_df_ms, long long* shift_df_launches, double* reduce_ms,
-                        long long* fp64_redone) {
+                        long long* fp64_redone, long long* guard_redone) {
   if (!ctx) return TRANSEC_EINVAL;
+  if (guard_redone) *guard_redone = ctx->sweep_guard_redone;
   if (stencil_df_ms) *stencil_df_ms = ctx->sweep_stencil_df_ms;
   if (stencil_df_launches) *stencil_df_launches = ctx->sweep_stencil_df_launches;
   if (shift_df_ms) *shift_df_ms = ctx->sweep_shift_df_ms;

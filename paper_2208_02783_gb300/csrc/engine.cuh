@@ -119,6 +119,7 @@ struct transec_ctx {
   double sweep_stencil_ms = 0, sweep_shift_ms = 0, sweep_update_ms = 0, sweep_reduce_ms = 0;
   long long sweep_stencil_launches = 0, sweep_shift_launches = 0;
   long long sweep_fp64_redone = 0;  // double-float results solved again in FP64
+  long long sweep_guard_redone = 0;  // sketch results computed again with a larger sketch
   double sweep_stencil_df_ms = 0, sweep_shift_df_ms = 0;  // the double-float runs' kernels
   long long sweep_stencil_df_launches = 0, sweep_shift_df_launches = 0;
 };

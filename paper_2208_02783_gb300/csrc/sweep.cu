@@ -956,7 +956,10 @@ __global__ void k_cplx_to_df(const double2* x, float4* y, long long n) {
 }
 
 template <int R, bool ISO>
-cudaError_t stencil_df_r(dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a, bool prepare) {
+cudaError_t stencil_df_r(dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a, bool prepare,
+                         int* blocks_per_sm) {
+  if (blocks_per_sm)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_stencil_df<R, ISO>, threads, smem);
   if (prepare) {
     // all of the SM's unified memory as shared memory (the z-ring is large)
     cudaError_t e = cudaFuncSetAttribute(k_stencil_df<R, ISO>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -969,24 +972,44 @@ cudaError_t stencil_df_r(dim3 grid, int threads, size_t smem, cudaStream_t s, co
 
 template <bool ISO>
 cudaError_t stencil_df_iso(int R, dim3 grid, int threads, size_t smem, cudaStream_t s, const StencilDfArgs& a,
-                           bool prepare) {
+                           bool prepare, int* bps) {
   switch (R) {
-    case 1: return stencil_df_r<1, ISO>(grid, threads, smem, s, a, prepare);
-    case 2: return stencil_df_r<2, ISO>(grid, threads, smem, s, a, prepare);
-    case 3: return stencil_df_r<3, ISO>(grid, threads, smem, s, a, prepare);
-    case 4: return stencil_df_r<4, ISO>(grid, threads, smem, s, a, prepare);
-    case 5: return stencil_df_r<5, ISO>(grid, threads, smem, s, a, prepare);
-    case 6: return stencil_df_r<6, ISO>(grid, threads, smem, s, a, prepare);
+    case 1: return stencil_df_r<1, ISO>(grid, threads, smem, s, a, prepare, bps);
+    case 2: return stencil_df_r<2, ISO>(grid, threads, smem, s, a, prepare, bps);
+    case 3: return stencil_df_r<3, ISO>(grid, threads, smem, s, a, prepare, bps);
+    case 4: return stencil_df_r<4, ISO>(grid, threads, smem, s, a, prepare, bps);
+    case 5: return stencil_df_r<5, ISO>(grid, threads, smem, s, a, prepare, bps);
+    case 6: return stencil_df_r<6, ISO>(grid, threads, smem, s, a, prepare, bps);
     default: return cudaErrorInvalidValue;
   }
 }
 
-// prepare = true sets the kernel's shared-memory limit; false launches it.  iso: the
-// three axes have the same spacing (one coefficient per distance)
+// prepare = true sets the kernel's shared-memory limit; false launches it; with
+// blocks_per_sm set, only the kernel's resident blocks per SM at (threads, smem) are
+// returned.  iso: the three axes have the same spacing (one coefficient per distance)
 cudaError_t stencil_df(int R, bool iso, dim3 grid, int threads, size_t smem, cudaStream_t s,
-                       const StencilDfArgs& a, bool prepare) {
-  return iso ? stencil_df_iso<true>(R, grid, threads, smem, s, a, prepare)
-             : stencil_df_iso<false>(R, grid, threads, smem, s, a, prepare);
+                       const StencilDfArgs& a, bool prepare, int* blocks_per_sm = nullptr) {
+  return iso ? stencil_df_iso<true>(R, grid, threads, smem, s, a, prepare, blocks_per_sm)
+             : stencil_df_iso<false>(R, grid, threads, smem, s, a, prepare, blocks_per_sm);
+}
+
+// Slabs per run for the double-float stencil when the caller sets no depth: the count
+// whose launch of S runs best fills whole waves of resident blocks, each slab paying a
+// 2R-plane prologue (about 3.6 planes of stencil time at order 12, measured).
+int df_slabs(int S, int nz, int resident) {
+  int best = 1;
+  double best_cost = 1e300;
+  for (int ns = 1; ns <= std::max(1, nz / 8); ++ns) {
+    const int D = (nz + ns - 1) / ns;
+    const long long blocks = (long long)S * ns;
+    const long long waves = (blocks + resident - 1) / resident;
+    const double cost = (double)waves * (D + 3.6);  // block-planes along the critical path
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = ns;
+    }
+  }
+  return best;
 }
 
 // ---------------------------------------------------------------------------------
@@ -1053,11 +1076,23 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   const long long n = g.n, nxy = g.nxy;
   const int nlp = (int)ctx->lplanes.size(), nrp = (int)ctx->rplanes.size();
   const long long no = (long long)std::max(nlp, nrp) * nxy;
-  // the double-float stencil spends a larger share on the 2R-plane prologue of a slab,
-  // so its default slab is deeper
-  const int slab = ctx->opts.slab > 0 ? ctx->opts.slab : (dfm ? 64 : 0);
-  const TileShape ts = choose_tiles(g, H, sizeof(double2), dfm ? kDfThreads : StencilMax<double>::threads,
-                                    ctx->opts.tile_y, slab);
+  // the double-float stencil's default depth fills whole waves of resident blocks
+  // (df_slabs); the FP64 stencil keeps the tile chooser's default
+  TileShape ts = choose_tiles(g, H, sizeof(double2), dfm ? kDfThreads : StencilMax<double>::threads,
+                              ctx->opts.tile_y, ctx->opts.slab > 0 ? ctx->opts.slab : (dfm ? 64 : 0));
+  bool iso = true;
+  for (int m = 1; m <= g.R; ++m) iso = iso && g.kx[m] == g.ky[m] && g.kx[m] == g.kz[m];
+  const size_t smem_df = stencil_df_smem(g.R, ts.TX, ts.TY, H, ts.threads);
+  if (dfm) {
+    MS_CK(stencil_df(g.R, iso, dim3(1), 0, smem_df, ctx->s, StencilDfArgs{}, true));
+    if (ctx->opts.slab <= 0) {
+      int bps = 0, sms = 0;
+      MS_CK(stencil_df(g.R, iso, dim3(1), ts.threads, smem_df, ctx->s, StencilDfArgs{}, false, &bps));
+      MS_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+      const int ns = df_slabs(S * ts.ntx * ts.nty, g.nz, std::max(1, bps) * std::max(1, sms));
+      ts = choose_tiles(g, H, sizeof(double2), kDfThreads, ctx->opts.tile_y, (g.nz + ns - 1) / ns);
+    }
+  }
   if (psym && (!dfm || ts.ntx != 1 || ts.nty != 1 || ts.TX != g.nx || ts.TY != g.ny))
     return ms_fail(ctx, TRANSEC_EINVAL, "P-symmetric runs need the double-float form and a plane in one tile");
   const int nblk_st = ts.ntx * ts.nty * ts.nslab;
@@ -1151,11 +1186,7 @@ int run_sweep(transec_ctx* ctx, const std::vector<MsItem>& items, const std::vec
   a.H = H; a.psym = psym ? 1 : 0; a.nx = g.nx; a.ny = g.ny; a.phase = ctx->d_phase;
   a.res_t = res_t; a.res_it = res_it; a.res_st = res_st;
 
-  const size_t smem_df = stencil_df_smem(g.R, ts.TX, ts.TY, H, ts.threads);
-  bool iso = true;
-  for (int m = 1; m <= g.R; ++m) iso = iso && g.kx[m] == g.ky[m] && g.kx[m] == g.kz[m];
-  if (dfm) MS_CK(stencil_df(g.R, iso, dim3(1), 0, smem_df, st, StencilDfArgs{}, true));
-  else MS_CK(prepare_stencil<double>(g.R, ts.smem));
+  if (!dfm) MS_CK(prepare_stencil<double>(g.R, ts.smem));
   StencilDfArgs da{};
   da.r = reinterpret_cast<const float4*>(B.R); da.q = reinterpret_cast<float4*>(B.Q); da.part = B.sig_part;
   da.slots = B.slots; da.escale = B.escale; da.phase = B.phase_df; da.v = B.v_df; da.gam = B.gam_df;
@@ -1694,6 +1725,39 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
         out.st[u] = o2.st[v];
         out.it[u] += o2.it[v];
         ctx->sweep_fp64_redone += 1;
+      }
+  }
+  // the a-posteriori check acting: results whose independent +-k estimates disagree by
+  // more than the guard are computed again with a sketch of twice the sizes
+  for (int round = 0; !psym && ctx->opts.sketch_guard > 0 && round < 3; ++round) {
+    std::vector<int> st2((size_t)nrep * ne, TRANSEC_OK);
+    bool any = false;
+    for (size_t u = 0; u < st2.size(); ++u)
+      if (out.st[u] == TRANSEC_OK && !(std::fabs(out.t[u] - out.tm[u]) <= ctx->opts.sketch_guard)) {
+        st2[u] = TRANSEC_ENOCONV;  // marks the result for failed_parts
+        any = true;
+      }
+    if (!any || (s_left >= kGnMaxL && s_right >= kGnMaxR)) break;
+    s_left = std::min(2 * s_left, kGnMaxL);
+    s_right = std::max(s_left, std::min(2 * s_right, kGnMaxR));
+    failed_parts(st2, nrep, ne, rows, ecols);
+    std::vector<double> e3;
+    std::vector<int> k3;
+    for (int s : ecols) e3.push_back(es[s]);
+    for (int r : rows) k3.push_back(hik[r]);
+    SweepOut o3;
+    rc = sketch_solve(ctx, e3, k3, s_left, s_right, splitmix64(seed + 0x9E37ULL * (round + 1)), o3);
+    if (rc != TRANSEC_OK) return rc;
+    for (size_t a = 0; a < rows.size(); ++a)
+      for (size_t b = 0; b < ecols.size(); ++b) {
+        const size_t u = (size_t)rows[a] * ne + ecols[b], v = a * ecols.size() + b;
+        if (st2[u] == TRANSEC_OK) continue;
+        out.it[u] += o3.it[v];
+        if (o3.st[v] != TRANSEC_OK) continue;  // keep the smaller sketch's estimate
+        out.t[u] = o3.t[v];
+        out.tm[u] = o3.tm[v];
+        out.rank[u] = o3.rank[v];
+        ctx->sweep_guard_redone += 1;
       }
   }
   int worst = TRANSEC_OK;

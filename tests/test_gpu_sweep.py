@@ -237,3 +237,31 @@ def test_psym_argument_checks():
             with pytest.raises(pkg.TransecError) as ei:
                 tr.transmission_sketch([0.3], [0], s_left=4, s_right=8)
             assert ei.value.status == pkg.EINVAL
+
+
+def test_sketch_guard_redoes_disagreeing_results():
+    """The a-posteriori check acting: with the guard below the two estimates' rounding
+    difference, every result is computed again with doubled sketches (counted in the
+    stats) and still matches dense LU; the default guard (1e-7) leaves these results
+    alone (their estimates agree to ~1e-12)."""
+    need_gpu()
+    kf = (0.23, -0.37)
+    inst = _inst(kf, seed=13, nx=6, ny=6, nz=44, order=8, ncap=9)
+    g = inst.grid
+    energies = np.linspace(0.2, 0.8, 4)
+    with context(inst, precision=2) as tr:
+        tr.stats_reset()
+        a = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=3)
+        ga = tr.sweep_stats()["guard_redone"]
+        tr.set_solver(sketch_guard=1e-300)
+        tr.stats_reset()
+        b = tr.transmission_sketch(energies, [0], s_left=8, s_right=16, seed=3)
+        gb = tr.sweep_stats()["guard_redone"]
+    assert ga == 0
+    assert gb >= energies.size
+    assert np.all(b["iters"] > a["iters"])
+    for r in (a, b):
+        assert np.all(r["status"] == 0)
+        for s, e in enumerate(energies):
+            tp, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf)
+            assert abs(r["T"][0, s] - tp) <= TOL_T
