@@ -287,8 +287,11 @@ int transec_stats_reset(transec_ctx* ctx);
  * ReLU, 2x2x2 average pooling, nearest 2x upsampling and skip concatenation, 4 input
  * channels (Re r, Im r, V, Gamma) and 2 outputs (Re e, Im e).  Its convolutions run as
  * BF16 tensor-core implicit GEMMs with FP32 accumulation (forward, data gradient,
- * weight gradient), trained with Adam on FP32 master weights.  A network is built for
- * one volume nx x ny x nz (each a multiple of 4).
+ * weight gradient), trained with Adam on FP32 master weights.  The forward and
+ * data-gradient convolutions use tcgen05 MMAs with the accumulator in tensor memory
+ * when a lateral plane of the level (with a one-voxel halo) fits the block's shared
+ * memory, mma.sync tiles otherwise; the weight gradient uses mma.sync.  A network is
+ * built for one volume nx x ny x nz (each a multiple of 4).
  */
 typedef struct transec_unet transec_unet;
 
@@ -307,9 +310,13 @@ int transec_unet_get_params(transec_unet* u, float* params);
 int transec_unet_forward(transec_unet* u, const float* in, float* out, int on_device);
 /* One training step on one volume: relative loss sum|y - t|^2 / sum|t|^2 against
  * target[v][0..1], backward, and an Adam update when lr > 0.  loss / grads (host, flat
- * layout) may be NULL.  Device or host arrays. */
+ * layout) may be NULL.  Device or host arrays.  forward and train_step return
+ * ETIMEOUT when a tcgen05 convolution gave up waiting for its MMAs (bounded wait). */
 int transec_unet_train_step(transec_unet* u, const float* in, const float* target, float lr,
                             float* loss, float* grads, int on_device);
+/* Convolution kernels: 0 (default) tcgen05 where the plane fits, else mma.sync; 1 the
+ * mma.sync kernels only.  Errors: EINVAL. */
+int transec_unet_set_path(transec_unet* u, int path);
 /* Volume the network was built for.  Any output may be NULL. */
 int transec_unet_dims(const transec_unet* u, int* nx, int* ny, int* nz);
 const char* transec_unet_last_error(const transec_unet* u);

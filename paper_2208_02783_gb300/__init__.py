@@ -20,7 +20,7 @@ from .binding import (  # noqa: F401
     transec_version, transec_fgmres_columns, transec_shifted_column, transec_shifted_columns,
     transec_sweep_stats, transec_transmission_sketch, transec_unet_create, transec_unet_destroy,
     transec_unet_dims, transec_unet_forward, transec_unet_get_params, transec_unet_n_params,
-    transec_unet_set_params, transec_unet_train_operator, transec_unet_train_step,
+    transec_unet_set_params, transec_unet_set_path, transec_unet_train_operator, transec_unet_train_step,
 )
 
 

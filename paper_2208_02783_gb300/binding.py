@@ -108,6 +108,7 @@ _SIGS = {
                                       C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                       C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "transec_unet_destroy": (None, [_P]),
+    "transec_unet_set_path": (C.c_int, [_P, C.c_int]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
 }
@@ -419,6 +420,11 @@ def transec_unet_get_params(u):
     out = np.zeros(transec_unet_n_params(u), np.float32)
     _ucheck(u, load().transec_unet_get_params(u, out.ctypes.data_as(C.c_void_p)), "transec_unet_get_params")
     return out
+
+
+def transec_unet_set_path(u, path):
+    """0: tcgen05 convolutions where the plane fits (default); 1: mma.sync only."""
+    _ucheck(u, load().transec_unet_set_path(u, int(path)), "transec_unet_set_path")
 
 
 def transec_unet_forward(u, x, y):

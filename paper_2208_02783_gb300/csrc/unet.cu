@@ -11,6 +11,7 @@
 
 #include "../../include/transec.h"
 #include "unet.cuh"
+#include "unet_tc.cuh"
 
 using namespace transec::unet;
 
@@ -57,6 +58,9 @@ struct transec_unet {
   float* bpart = nullptr;   // per-block bias-gradient partial sums
   float* in_buf = nullptr;
   cudaStream_t s = nullptr;
+  int sms = 0;            // SMs of the device
+  int path = 0;           // 0: tensor-core (tcgen05) convolutions where the plane fits; 1: mma.sync only
+  int* d_err = nullptr;   // set by a tcgen05 convolution whose wait timed out
   std::string err;
 };
 
@@ -102,9 +106,27 @@ void conv(transec_unet* u, int l, const bf16* x, bf16* y, float* yf, long long n
     a.cin = L.cout_p; a.cout = L.cin_p; a.relu = 0;
   }
   a.nx = nx; a.ny = ny; a.nz = nz; a.nvox = nvox;
+  const ConvTcPlan p = u->path == 0 ? conv_tc_plan(nx, ny, nz, a.cin, a.cout, u->sms) : ConvTcPlan{};
+  if (p.ok) {
+    ConvTcArgs ta{};
+    ta.x = a.x; ta.w = a.w; ta.b = a.b; ta.y = a.y; ta.yf = a.yf; ta.err = u->d_err;
+    ta.cin = a.cin; ta.cout = a.cout; ta.nx = nx; ta.ny = ny; ta.nz = nz; ta.relu = a.relu;
+    ta.bz = p.bz; ta.kc = p.kc; ta.mt = p.mt; ta.tcols = p.tcols; ta.npos = p.npos;
+    k_conv_tc<<<(unsigned)((nz + p.bz - 1) / p.bz), 128, p.smem, u->s>>>(ta);
+    return;
+  }
   const size_t smem = conv_smem_bytes(a.cin);
   const unsigned bricks = (unsigned)(((nx + kBX - 1) / kBX) * ((ny + kBY - 1) / kBY) * ((nz + kBZ - 1) / kBZ));
   k_conv<<<dim3(bricks, (unsigned)(a.cout / 16)), 128, smem, u->s>>>(a);
+}
+
+// ETIMEOUT (and the flag cleared) when a tensor-core convolution gave up waiting
+int check_tc_error(transec_unet* u) {
+  int h = 0;
+  UCK(cudaMemcpy(&h, u->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return TRANSEC_OK;
+  UCK(cudaMemset(u->d_err, 0, sizeof(int)));
+  return ufail(u, TRANSEC_ETIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
 }
 
 int wgrad_chunk(long long nvox) {
@@ -246,6 +268,13 @@ int transec_unet_create(transec_unet** out, int device, int nx, int ny, int nz, 
   fl(&u->in_buf, u->n0 * 4);
   if (rc == TRANSEC_OK && cudaMalloc(&u->sums, 2 * sizeof(double)) != cudaSuccess) rc = TRANSEC_ENOMEM;
   if (rc == TRANSEC_OK && cudaMalloc(&u->lpart, 512 * sizeof(double)) != cudaSuccess) rc = TRANSEC_ENOMEM;
+  if (rc == TRANSEC_OK && cudaMalloc(&u->d_err, sizeof(int)) != cudaSuccess) rc = TRANSEC_ENOMEM;
+  if (rc == TRANSEC_OK && cudaMemset(u->d_err, 0, sizeof(int)) != cudaSuccess) rc = TRANSEC_ECUDA;
+  if (rc == TRANSEC_OK && cudaDeviceGetAttribute(&u->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    rc = TRANSEC_ECUDA;
+  if (rc == TRANSEC_OK &&
+      cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax) != cudaSuccess)
+    rc = TRANSEC_ECUDA;
   {
     // the largest [chunks][27][cout][cin] slice set over the layers (level of each layer
     // from the execution order: e1*, d1*, out at full size; e2*, d2* at 1/8; e3* at 1/64)
@@ -368,7 +397,7 @@ int transec_unet_forward(transec_unet* u, const float* in, float* out, int on_de
   UCK(cudaMemcpy2DAsync(out, 2 * sizeof(float), u->out, 16 * sizeof(float), 2 * sizeof(float), u->n0,
                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, u->s));
   UCK(cudaStreamSynchronize(u->s));
-  return TRANSEC_OK;
+  return check_tc_error(u);
 }
 
 // one step: forward on `in`, relative loss against `target` ([n0][2]), backward; with
@@ -417,7 +446,14 @@ int transec_unet_train_step(transec_unet* u, const float* in, const float* targe
   if (tbuf) cudaFree(tbuf);
   if (rc == TRANSEC_OK && cudaStreamSynchronize(u->s) != cudaSuccess) rc = TRANSEC_ECUDA;
   if (rc != TRANSEC_OK) cudaGetLastError();
+  if (rc == TRANSEC_OK) rc = check_tc_error(u);
   return rc;
+}
+
+int transec_unet_set_path(transec_unet* u, int path) {
+  if (!u || path < 0 || path > 1) return TRANSEC_EINVAL;
+  u->path = path;
+  return TRANSEC_OK;
 }
 
 int transec_unet_dims(const transec_unet* u, int* nx, int* ny, int* nz) {
@@ -439,7 +475,8 @@ void transec_unet_destroy(transec_unet* u) {
                   (void*)u->p2, (void*)u->e3a, (void*)u->a3, (void*)u->u3, (void*)u->cat2, (void*)u->d2a,
                   (void*)u->d2, (void*)u->u2, (void*)u->cat1, (void*)u->d1a, (void*)u->d1, (void*)u->out,
                   (void*)u->gA, (void*)u->gB, (void*)u->gC, (void*)u->gSkip1, (void*)u->gSkip2,
-                  (void*)u->sums, (void*)u->lpart, (void*)u->wpart, (void*)u->bpart, (void*)u->in_buf})
+                  (void*)u->sums, (void*)u->lpart, (void*)u->wpart, (void*)u->bpart, (void*)u->in_buf,
+                  (void*)u->d_err})
     if (q) cudaFree(q);
   if (u->s) cudaStreamDestroy(u->s);
   cudaGetLastError();

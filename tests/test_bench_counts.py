@@ -73,5 +73,6 @@ def test_sketch_plan_is_seeded_and_in_range():
     a = bench.sketch_plan(256, reps, 40, 16)
     b = bench.sketch_plan(256, reps, 40, 16)
     assert a == b
+    assert bench.sketch_plan(256, reps, 7, 16) == a[:7]  # a step's window is independent of the count
     assert all(k in reps and 0 <= e <= 256 - 16 for k, e in a)
     assert len({k for k, _ in a}) > 5 and len({e for _, e in a}) > 10

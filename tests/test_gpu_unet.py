@@ -24,6 +24,10 @@ The volumes 8 x 12 x 16 and 8 x 8 x 20 make the coarser levels (6 x 4, 3 x 2 in 
 against oracle.unet.adam_step fed with the GPU's own gradients, three steps, element
 by element.  The reference itself is pinned by finite differences and closed forms in
 tests/test_oracle_unet.py.
+
+Both convolution paths are checked: the tcgen05 kernels (MMAs from shared-memory
+descriptors, accumulator in tensor memory; used where a lateral plane fits) and the
+mma.sync kernels (transec_unet_set_path 1).
 """
 
 import numpy as np
@@ -35,6 +39,7 @@ from oracle import unet as ref
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(8, 8, 16), (8, 12, 16), (8, 8, 20)]  # nz, ny, nx
+PATHS = [0, 1]  # tcgen05 where the plane fits, mma.sync only
 
 
 def _unflatten(flat):
@@ -56,9 +61,10 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def _setup(pkg, shape, seed=5):
+def _setup(pkg, shape, seed=5, path=0):
     nz, ny, nx = shape
     u = pkg.binding.transec_unet_create(0, nx, ny, nz, seed)
+    pkg.binding.transec_unet_set_path(u, path)
     rng = np.random.default_rng(seed)
     x = rng.normal(size=shape + (4,)).astype(np.float32)
     t = rng.normal(size=shape + (2,)).astype(np.float32)
@@ -72,11 +78,12 @@ def _setup(pkg, shape, seed=5):
     return u, x, t, params
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("shape", SHAPES)
-def test_forward_matches_reference_elementwise(shape):
+def test_forward_matches_reference_elementwise(shape, path):
     need_gpu()
     pkg = library()
-    u, x, t, params = _setup(pkg, shape)
+    u, x, t, params = _setup(pkg, shape, path=path)
     try:
         y = np.zeros(shape + (2,), np.float32)
         pkg.binding.transec_unet_forward(u, x, y)
@@ -90,11 +97,12 @@ def test_forward_matches_reference_elementwise(shape):
         pkg.binding.transec_unet_destroy(u)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("shape", SHAPES)
-def test_gradients_match_reference_elementwise(shape):
+def test_gradients_match_reference_elementwise(shape, path):
     need_gpu()
     pkg = library()
-    u, x, t, params = _setup(pkg, shape, seed=6)
+    u, x, t, params = _setup(pkg, shape, seed=6, path=path)
     try:
         # the backward starts from the loss gradient of the GPU's own output, so that the
         # comparison covers the backward pass alone (the forward is checked above)
