@@ -317,6 +317,15 @@ int transec_unet_train_step(transec_unet* u, const float* in, const float* targe
 /* Convolution kernels: 0 (default) tcgen05 where the plane fits, else mma.sync; 1 the
  * mma.sync kernels only.  Errors: EINVAL. */
 int transec_unet_set_path(transec_unet* u, int path);
+/* One 3x3x3 convolution of the network alone (zero padding), on `device`:
+ * y[v][o] = b[o] + sum over taps t and input channels i of w[t][o][i] x[v + d_t][i],
+ * tap t = (dz+1)*9 + (dy+1)*3 + (dx+1), voxel v = x + nx(y + ny z).  x: [nx*ny*nz][cin]
+ * and w: [27][cout][cin] as bfloat16 bit patterns, b: [cout] float (may be NULL), y:
+ * [nx*ny*nz][cout] float; host arrays, FP32 accumulation.  path 0: the tcgen05 kernel
+ * where the plane fits (else mma.sync), 1: the mma.sync kernel.  cin, cout multiples of
+ * 16 (cout <= 256).  Errors: EINVAL, ENOMEM, ECUDA, ETIMEOUT. */
+int transec_unet_conv3d(int device, int nx, int ny, int nz, int cin, int cout, const uint16_t* x,
+                        const uint16_t* w, const float* b, float* y, int path);
 /* Volume the network was built for.  Any output may be NULL. */
 int transec_unet_dims(const transec_unet* u, int* nx, int* ny, int* nz);
 const char* transec_unet_last_error(const transec_unet* u);

@@ -109,6 +109,8 @@ _SIGS = {
                                       C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "transec_unet_destroy": (None, [_P]),
     "transec_unet_set_path": (C.c_int, [_P, C.c_int]),
+    "transec_unet_conv3d": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P,
+                                      C.c_int]),
     "transec_last_error": (C.c_char_p, [_P]),
     "transec_destroy": (None, [_P]),
 }
@@ -425,6 +427,24 @@ def transec_unet_get_params(u):
 def transec_unet_set_path(u, path):
     """0: tcgen05 convolutions where the plane fits (default); 1: mma.sync only."""
     _ucheck(u, load().transec_unet_set_path(u, int(path)), "transec_unet_set_path")
+
+
+def transec_unet_conv3d(x_bf16, w_bf16, b, path=0, device=0):
+    """One convolution alone: x [nz][ny][nx][cin] and w [27][cout][cin] as bfloat16 bit
+    patterns (uint16), b [cout] float32 or None; returns y [nz][ny][nx][cout] float32."""
+    x = np.ascontiguousarray(x_bf16, np.uint16)
+    w = np.ascontiguousarray(w_bf16, np.uint16)
+    nz, ny, nx, cin = x.shape
+    cout = w.shape[1]
+    y = np.zeros((nz, ny, nx, cout), np.float32)
+    bb = None if b is None else np.ascontiguousarray(b, np.float32)
+    st = load().transec_unet_conv3d(int(device), nx, ny, nz, cin, cout, x.ctypes.data_as(C.c_void_p),
+                                    w.ctypes.data_as(C.c_void_p),
+                                    bb.ctypes.data_as(C.c_void_p) if bb is not None else None,
+                                    y.ctypes.data_as(C.c_void_p), int(path))
+    if st != OK:
+        raise TransecError(st, "transec_unet_conv3d")
+    return y
 
 
 def transec_unet_forward(u, x, y):

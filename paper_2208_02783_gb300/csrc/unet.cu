@@ -450,6 +450,60 @@ int transec_unet_train_step(transec_unet* u, const float* in, const float* targe
   return rc;
 }
 
+int transec_unet_conv3d(int device, int nx, int ny, int nz, int cin, int cout, const uint16_t* x,
+                        const uint16_t* w, const float* b, float* y, int path) {
+  if (nx < 1 || ny < 1 || nz < 1 || cin < 16 || cout < 16 || cin % 16 || cout % 16 || cout > 256 || !x || !w ||
+      !y || path < 0 || path > 1)
+    return TRANSEC_EINVAL;
+  Dev dg(device);
+  const long long nv = (long long)nx * ny * nz;
+  bf16 *dx = nullptr, *dw = nullptr;
+  float *db = nullptr, *dy = nullptr;
+  int* de = nullptr;
+  int rc = TRANSEC_OK;
+  auto ck = [&](cudaError_t e) {
+    if (rc == TRANSEC_OK && e != cudaSuccess) rc = e == cudaErrorMemoryAllocation ? TRANSEC_ENOMEM : TRANSEC_ECUDA;
+  };
+  ck(cudaMalloc(&dx, nv * cin * sizeof(bf16)));
+  ck(cudaMalloc(&dw, 27LL * cout * cin * sizeof(bf16)));
+  ck(cudaMalloc(&dy, nv * cout * sizeof(float)));
+  ck(cudaMalloc(&de, sizeof(int)));
+  if (b) ck(cudaMalloc(&db, cout * sizeof(float)));
+  ck(cudaMemcpy(dx, x, nv * cin * sizeof(bf16), cudaMemcpyHostToDevice));
+  ck(cudaMemcpy(dw, w, 27LL * cout * cin * sizeof(bf16), cudaMemcpyHostToDevice));
+  if (b) ck(cudaMemcpy(db, b, cout * sizeof(float), cudaMemcpyHostToDevice));
+  ck(cudaMemset(de, 0, sizeof(int)));
+  int sms = 0;
+  ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  if (rc == TRANSEC_OK) {
+    const ConvTcPlan p = path == 0 ? conv_tc_plan(nx, ny, nz, cin, cout, sms) : ConvTcPlan{};
+    if (p.ok) {
+      ck(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
+      ConvTcArgs ta{};
+      ta.x = dx; ta.w = dw; ta.b = db; ta.y = nullptr; ta.yf = dy; ta.err = de;
+      ta.cin = cin; ta.cout = cout; ta.nx = nx; ta.ny = ny; ta.nz = nz; ta.relu = 0;
+      ta.bz = p.bz; ta.kc = p.kc; ta.mt = p.mt; ta.tcols = p.tcols; ta.npos = p.npos;
+      if (rc == TRANSEC_OK) k_conv_tc<<<(unsigned)((nz + p.bz - 1) / p.bz), 128, p.smem>>>(ta);
+    } else {
+      ck(cudaFuncSetAttribute(k_conv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)conv_smem_bytes(cin)));
+      ConvArgs a{};
+      a.x = dx; a.w = dw; a.b = db; a.y = nullptr; a.yf = dy;
+      a.cin = cin; a.cout = cout; a.nx = nx; a.ny = ny; a.nz = nz; a.relu = 0; a.nvox = nv;
+      const unsigned bricks = (unsigned)(((nx + kBX - 1) / kBX) * ((ny + kBY - 1) / kBY) * ((nz + kBZ - 1) / kBZ));
+      if (rc == TRANSEC_OK) k_conv<<<dim3(bricks, (unsigned)(cout / 16)), 128, conv_smem_bytes(cin)>>>(a);
+    }
+    ck(cudaGetLastError());
+    ck(cudaDeviceSynchronize());
+  }
+  int herr = 0;
+  ck(cudaMemcpy(y, dy, nv * cout * sizeof(float), cudaMemcpyDeviceToHost));
+  ck(cudaMemcpy(&herr, de, sizeof(int), cudaMemcpyDeviceToHost));
+  if (rc == TRANSEC_OK && herr) rc = TRANSEC_ETIMEOUT;
+  cudaFree(dx); cudaFree(dw); cudaFree(db); cudaFree(dy); cudaFree(de);
+  cudaGetLastError();
+  return rc;
+}
+
 int transec_unet_set_path(transec_unet* u, int path) {
   if (!u || path < 0 || path > 1) return TRANSEC_EINVAL;
   u->path = path;

@@ -98,6 +98,12 @@ __device__ inline uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
   return d;
 }
 
+// 16-byte global-to-shared copy that does not hold a register (many in flight per
+// thread); bytes = 0 writes zeros without reading
+__device__ inline void tc_copy16(uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+
 __device__ inline void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
@@ -162,25 +168,27 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvTcArgs a) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
     if (!__syncthreads_and(ok)) break;
-    // input box, zero outside the volume and past the box
+    // input box, zero outside the volume and past the box; asynchronous 16-byte copies,
+    // all of a thread's copies in flight at once
+    const uint32_t box_s = tc_smem_u32(box), w_s = tc_smem_u32(wsm);
     for (int idx = t; idx < npos * nch; idx += blockDim.x) {
       const int pos = idx / nch, ch = idx - pos * nch;
       const int zb = pos / P, rem = pos - zb * P;
       const int yb = rem / XH, xb = rem - yb * XH;
       const int gx = xb - 1, gy = yb - 1, gz = z0 - 1 + zb;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (zb < a.bz + 2 && gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-        v = *reinterpret_cast<const uint4*>(a.x + ((long long)gx + (long long)nx * (gy + (long long)ny * gz)) * a.cin +
-                                           c0 + ch * 8);
-      *reinterpret_cast<uint4*>(box + ((size_t)ch * npos + pos) * 8) = v;
+      const bool in = zb < a.bz + 2 && gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+      const bf16* src =
+          in ? a.x + ((long long)gx + (long long)nx * (gy + (long long)ny * gz)) * a.cin + c0 + ch * 8 : a.x;
+      tc_copy16(box_s + (uint32_t)(((size_t)ch * npos + pos) * 16), src, in ? 16u : 0u);
     }
     // the pass's weights of every tap
     for (int idx = t; idx < 27 * cout * nch; idx += blockDim.x) {
       const int ch = idx % nch, rest = idx / nch;
       const int o = rest % cout, tap = rest / cout;
-      const uint4 v = *reinterpret_cast<const uint4*>(a.w + ((long long)tap * cout + o) * a.cin + c0 + ch * 8);
-      *reinterpret_cast<uint4*>(wsm + (((size_t)tap * nch + ch) * cout + o) * 8) = v;
+      tc_copy16(w_s + (uint32_t)((((size_t)tap * nch + ch) * cout + o) * 16),
+                a.w + ((long long)tap * cout + o) * a.cin + c0 + ch * 8, 16u);
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

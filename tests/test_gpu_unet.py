@@ -27,7 +27,14 @@ tests/test_oracle_unet.py.
 
 Both convolution paths are checked: the tcgen05 kernels (MMAs from shared-memory
 descriptors, accumulator in tensor memory; used where a lateral plane fits) and the
-mma.sync kernels (transec_unet_set_path 1).
+mma.sync kernels (transec_unet_set_path 1).  Each kernel alone is checked bit for bit
+on small-integer data (test_single_convolution_exact), where every sum is exact in
+FP32; in the network the two kernels' FP32 sums can differ in their last bits (the
+tcgen05 kernel takes wide inputs in channel passes, so its accumulation order differs),
+and the bfloat16 values that the two round to different neighbours reach the gradients
+through the backward pass (measured relative L2 error of the parameter gradients against the reference up
+to 1.6 % on the 8 x 8 x 20 volume with the tcgen05 kernels, 0.6 % with mma.sync), so
+the norm bar of the gradients is 2e-2; the element bars are the same for both.
 """
 
 import numpy as np
@@ -127,7 +134,7 @@ def test_gradients_match_reference_elementwise(shape, path):
         print("max error / element bar:", worst)
         print("relative L2 error:", rel)
         assert max(worst.values()) <= 1.0, worst
-        assert max(rel.values()) <= 1e-2, rel
+        assert max(rel.values()) <= 2e-2, rel
     finally:
         pkg.binding.transec_unet_destroy(u)
 
@@ -157,6 +164,38 @@ def test_adam_steps_match_reference():
             p = got
     finally:
         pkg.binding.transec_unet_destroy(u)
+
+
+CONV_CASES = [((8, 8, 16), 16, 16), ((8, 8, 20), 48, 16), ((4, 4, 10), 96, 32), ((4, 4, 10), 32, 96),
+              ((2, 2, 5), 64, 64), ((2, 3, 7), 16, 48), ((6, 20, 20), 64, 32)]  # (nz, ny, nx), cin, cout
+
+
+def _bf16_bits(a):
+    """bfloat16 bit patterns of float32 values that bfloat16 holds exactly."""
+    u = np.ascontiguousarray(a, np.float32).view(np.uint32)
+    assert np.all(u & 0xFFFF == 0)
+    return (u >> 16).astype(np.uint16)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("case", CONV_CASES)
+def test_single_convolution_exact(case, path):
+    """One convolution through each kernel with small-integer inputs and weights: every
+    product and partial sum is an integer below 2^24, exact in FP32 in any order, so the
+    output must equal the oracle's float64 convolution bit for bit.  A wrong tap,
+    channel, channel pass, halo cell or tile row shows as a mismatch.  The cases cover
+    one and several channel passes, N = 16 to 96, ragged and odd lateral sizes and a
+    20 x 20 plane."""
+    need_gpu()
+    pkg = library()
+    shape, cin, cout = case
+    rng = np.random.default_rng(cin * 131 + cout)
+    x = rng.integers(-2, 3, shape + (cin,)).astype(np.float32)
+    w = rng.integers(-2, 3, (27, cout, cin)).astype(np.float32)
+    b = rng.integers(-3, 4, cout).astype(np.float32)
+    y = pkg.binding.transec_unet_conv3d(_bf16_bits(x), _bf16_bits(w), b, path=path)
+    want = ref.conv3d(x.astype(np.float64), w.astype(np.float64), b.astype(np.float64))
+    assert np.array_equal(y, want.astype(np.float32)), float(np.abs(y - want).max())
 
 
 def test_training_reduces_loss():
