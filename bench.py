@@ -816,7 +816,8 @@ def run_learned(args):
                          "its weights every Arnoldi step)"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "whole forward (11 k_conv launches + pool/upsample/concat)",
+                     "kernel": "whole forward (11 convolutions: k_conv_tc on tcgen05 where the level's plane fits, else "
+                               "k_conv on mma.sync; + pool/upsample/concat)",
                      "flops_algorithmic": fl_alg, "flops_padded_channels": fl_pad,
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops (measured cuBLAS burst)"},
         "e2e": {"value": n / (e2e_ms / 1e3), "unit": "voxels/s", "h2d_bytes_per_step": n * 16,
