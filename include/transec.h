@@ -448,6 +448,26 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
                                 int* iters_out);
 
 /*
+ * The paper's eigen route, its per-energy stage (Sec. II.A, Eqs.
+ * transmission-eigenbasis, Gamma-tilde, G-diag; Sec. II.B; Sec. II.D's truncation to a
+ * fraction of the eigenpairs): T(E, k) from p eigenpairs of B(k) = H_k - i Gamma,
+ *   T(E) = 4 sum_{m,n} conj(g_m) g_n Rt[m, n] Lt[n, m],  g_n = 1/(E - lambda_n),
+ *   Rt = V^H Gamma_R V,  Lt = W^T Gamma_L conj(W),
+ * with V the right eigenvectors and W the left ones (W^T B = diag(lambda) W^T),
+ * normalised so that W^T V = 1 on the full grid (W are the right eigenvectors of
+ * B(-k)).  The caller supplies the eigensolution (the library does not compute it):
+ * lambda [p] complex (interleaved re, im); v_right [n_R][p] complex, the rows of V on
+ * the right-CAP support and w_left [n_L][p] complex, the rows of W on the left-CAP
+ * support, each support in grid order (the planes with Gamma > 0 ascending, x fastest
+ * within a plane; n_R = right-CAP planes x nx ny).  With every eigenpair the result is
+ * the exact T(E, k); with the p nearest the energies it is the paper's truncated sum.
+ * T_out [ne].  Host arrays; 1 <= p <= 10240.  Errors: EINVAL, ESTATE (CAPs not set),
+ * ENOMEM, ECUDA.
+ */
+int transec_eigen_transmission(transec_ctx* ctx, int p, const double* lambda, const double* v_right,
+                               const double* w_left, int ne, const double* energies, double* T_out);
+
+/*
  * Counters of the multi-shift engine since the last transec_stats_reset: seed
  * iterations summed over runs, per-shift point updates (kept points x halves x
  * iterations of each shift), with opts.profile set the event-timed stencil and

@@ -21,6 +21,7 @@ from .binding import (  # noqa: F401
     transec_sweep_stats, transec_transmission_sketch, transec_unet_create, transec_unet_destroy,
     transec_unet_dims, transec_unet_forward, transec_unet_get_params, transec_unet_n_params,
     transec_unet_set_params, transec_unet_set_path, transec_unet_train_operator, transec_unet_train_step,
+    transec_eigen_transmission,
 )
 
 
@@ -124,6 +125,10 @@ class Transec:
         """One left-CAP column at many energies in one multi-shift Krylov run."""
         t, tm, it, st = transec_shifted_column(self.ctx, energies, ik, col)
         return {"t": t, "t_minus": tm, "iters": it, "status": st}
+
+    def eigen_transmission(self, lam, v_right, w_left, energies):
+        """T(E, k) by the paper's eigenbasis trace from a supplied (partial) eigensolution."""
+        return transec_eigen_transmission(self.ctx, lam, v_right, w_left, energies)
 
     def shifted_columns(self, energies, ik, cols):
         """Sampled left-CAP columns, each at every energy of the window, by the

@@ -109,6 +109,7 @@ _SIGS = {
                                       C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "transec_unet_destroy": (None, [_P]),
     "transec_unet_set_path": (C.c_int, [_P, C.c_int]),
+    "transec_eigen_transmission": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, _P, _P]),
     "transec_unet_conv3d": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P,
                                       C.c_int]),
     "transec_last_error": (C.c_char_p, [_P]),
@@ -422,6 +423,24 @@ def transec_unet_get_params(u):
     out = np.zeros(transec_unet_n_params(u), np.float32)
     _ucheck(u, load().transec_unet_get_params(u, out.ctypes.data_as(C.c_void_p)), "transec_unet_get_params")
     return out
+
+
+def transec_eigen_transmission(ctx, lam, v_right, w_left, energies):
+    """T(E, k) from p eigenpairs: lam [p] complex, v_right [n_R][p] and w_left [n_L][p]
+    complex (rows of the right / left eigenvectors on the right / left CAP supports)."""
+    lam = np.ascontiguousarray(lam, np.complex128)
+    vr = np.ascontiguousarray(v_right, np.complex128)
+    wl = np.ascontiguousarray(w_left, np.complex128)
+    e = np.ascontiguousarray(energies, np.float64)
+    t = np.zeros(e.size)
+    p = lam.size
+    if vr.shape[1] != p or wl.shape[1] != p:
+        raise ValueError("eigenvector arrays need p columns")
+    st = load().transec_eigen_transmission(ctx, p, lam.ctypes.data_as(C.c_void_p), vr.ctypes.data_as(C.c_void_p),
+                                           wl.ctypes.data_as(C.c_void_p), e.size, e.ctypes.data_as(C.c_void_p),
+                                           t.ctypes.data_as(C.c_void_p))
+    _check(ctx, st, "transec_eigen_transmission")
+    return t
 
 
 def transec_unet_set_path(u, path):
