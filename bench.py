@@ -701,6 +701,78 @@ def run_sketch(args):
     return 0
 
 
+def run_eigen_stage(args):
+    """The paper's eigen route, its per-energy stage, on the bulk Cu cell: the transformed
+    CAPs (two weighted Gram matrices of p eigenvectors' rows on the 25 600-point CAP
+    supports) and the eigen-sum T(E) for the workload's 256 energies, from a supplied
+    eigensolution (random unit-modulus rows and eigenvalues near E_F: the stage's cost
+    does not depend on the values).  Timed through the public call with host arrays
+    (e2e); kernel times from a profiled call."""
+    import torch
+
+    from workloads import cu_bulk
+    import paper_2208_02783_gb300 as pkg
+    from paper_2208_02783_gb300 import build
+
+    pkg.load(build.build())
+    inst = cu_bulk()
+    g = inst.grid
+    p = args.items or 1024
+    rng = np.random.default_rng(11)
+    nr = int(np.count_nonzero(inst.gamma_r)) * g.nxy
+    nl = int(np.count_nonzero(inst.gamma_l)) * g.nxy
+    vr = np.exp(2j * np.pi * rng.random((nr, p))) / np.sqrt(nr)
+    wl = np.exp(2j * np.pi * rng.random((nl, p))) / np.sqrt(nl)
+    lam = inst.fermi + rng.uniform(-0.3, 0.3, p) - 1j * rng.uniform(1e-3, 5e-2, p)
+    en = inst.energies.astype(np.float64)
+    tr = pkg.Transec.from_instance(inst, device=0)
+    for _ in range(max(3, args.warmup)):
+        tr.eigen_transmission(lam, vr, wl, en)
+    torch.cuda.synchronize()
+    steps = max(1, args.steps)
+    clocks = Clocks(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        tr.eigen_transmission(lam, vr, wl, en)
+    dt = (time.perf_counter() - t0) / steps
+    clk = clocks.stop()
+    tr.set_solver(profile=1)
+    tr.stats_reset()
+    tr.eigen_transmission(lam, vr, wl, en)
+    es = pkg.binding.transec_eigen_stats(tr.ctx)
+    tr.set_solver(profile=0)
+    tr.close()
+    gram_flops = 8.0 * p * p * (nr + nl)
+    sum_flops = 8.0 * p * p * en.size
+    kern_s = (es["gram_ms"] + es["sum_ms"]) / 1e3
+    achieved = gram_flops / (es["gram_ms"] / 1e3) / 1e12
+    line = {
+        "metric": "eigen route, per-energy stage: T(E) values per second from a supplied eigensolution",
+        "value": en.size / dt, "unit": "T(E) values/s", "n_gpus": 1, "steps": steps, "warmup": max(3, args.warmup),
+        "ms_per_step": 1e3 * dt, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c128", "data": "synthetic",
+        "config": {"workload": WORKLOAD + f"; {p} eigenpairs, {en.size} energies",
+                   "step": "transformed CAPs (Gram matrices over 25 600 + 25 600 CAP rows) and the eigen-sum "
+                           "for every energy of the window",
+                   "kernel_ms": es},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                     "kernel": "k_eig_gram (complex FP64 Gram matrices, 16 x 16 shared-memory tiles)",
+                     "flops": {"gram": gram_flops, "sum": sum_flops},
+                     "sum_kernel_tflops": sum_flops / (es["sum_ms"] / 1e3) / 1e12 if es["sum_ms"] > 0 else None,
+                     "peak_source": "derived: 2 FP64 FMA/clk/SM x 152 SMs x 2070 MHz"},
+        "e2e": {"value": en.size / dt, "unit": "T(E) values/s",
+                "h2d_bytes_per_step": int((nr + nl) * p * 16 + p * 16 + en.size * 8),
+                "d2h_bytes_per_step": int(en.size * 8),
+                "kernel_share": kern_s / dt},
+        "gpu_launches": 3 * steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 UNET_LAYERS = [(4, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 64, 2),
                (96, 32, 1), (32, 32, 1), (48, 16, 0), (16, 16, 0), (16, 2, 0)]  # (cin, cout, level)
 
@@ -869,7 +941,8 @@ def main():
     ap.add_argument("--psym", action="store_true",
                     help="sketch forms: P-symmetric COCG runs (needs --workload cu_bulk_ideal)")
     ap.add_argument("--workload", default="cu_bulk",
-                    choices=["cu_bulk", "cu_bulk_ideal", "rh_point_contact", "uneven_batch", "learned"],
+                    choices=["cu_bulk", "cu_bulk_ideal", "rh_point_contact", "uneven_batch", "learned",
+                             "eigen_stage"],
                     help="rh_point_contact: the 60x60x512 Rh point contact (use --items 16); "
                          "uneven_batch: the 96-cell mixed batch, batched vs looped per cell; "
                          "learned: the U-Net preconditioner's forward and FGMRES gain")
@@ -880,6 +953,8 @@ def main():
         return run_uneven_batch(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "eigen_stage":
+        return run_eigen_stage(args)
     if args.form in ("sketch", "sketch_fp64"):
         return run_sketch(args)
 

@@ -466,6 +466,10 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
  */
 int transec_eigen_transmission(transec_ctx* ctx, int p, const double* lambda, const double* v_right,
                                const double* w_left, int ne, const double* energies, double* T_out);
+/* With opts.profile set, the event-timed ms since the last transec_stats_reset of the
+ * eigen route's two Gram-matrix launches and of its eigen-sum launch.  Either output
+ * may be NULL. */
+int transec_eigen_stats(const transec_ctx* ctx, double* gram_ms, double* sum_ms);
 
 /*
  * Counters of the multi-shift engine since the last transec_stats_reset: seed

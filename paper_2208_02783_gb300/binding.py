@@ -110,6 +110,7 @@ _SIGS = {
     "transec_unet_destroy": (None, [_P]),
     "transec_unet_set_path": (C.c_int, [_P, C.c_int]),
     "transec_eigen_transmission": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, _P, _P]),
+    "transec_eigen_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "transec_unet_conv3d": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P,
                                       C.c_int]),
     "transec_last_error": (C.c_char_p, [_P]),
@@ -441,6 +442,12 @@ def transec_eigen_transmission(ctx, lam, v_right, w_left, energies):
                                            t.ctypes.data_as(C.c_void_p))
     _check(ctx, st, "transec_eigen_transmission")
     return t
+
+
+def transec_eigen_stats(ctx) -> dict:
+    a, b = C.c_double(), C.c_double()
+    _check(ctx, load().transec_eigen_stats(ctx, C.byref(a), C.byref(b)), "transec_eigen_stats")
+    return {"gram_ms": a.value, "sum_ms": b.value}
 
 
 def transec_unet_set_path(u, path):

@@ -1470,6 +1470,8 @@ int transec_stats_reset(transec_ctx* ctx) {
   ctx->sweep_stencil_launches = ctx->sweep_shift_launches = 0;
   ctx->sweep_fp64_redone = 0;
   ctx->sweep_guard_redone = 0;
+  ctx->eig_gram_ms = 0;
+  ctx->eig_sum_ms = 0;
   ctx->sweep_stencil_df_ms = ctx->sweep_shift_df_ms = 0;
   ctx->sweep_stencil_df_launches = ctx->sweep_shift_df_launches = 0;
   return TRANSEC_OK;

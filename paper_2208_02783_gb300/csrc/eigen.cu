@@ -173,22 +173,43 @@ int transec_eigen_transmission(transec_ctx* ctx, int p, const double* lambda, co
   }
   if (rc == TRANSEC_OK) {
     const dim3 gg((unsigned)((p + kGT - 1) / kGT), (unsigned)((p + kGT - 1) / kGT));
+    const bool prof = ctx->opts.profile != 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    if (prof)
+      for (auto& e : ev) ck(cudaEventCreate(&e));
+    if (prof && rc == TRANSEC_OK) cudaEventRecord(ev[0], s);
     k_eig_gram<<<gg, dim3(kGT, kGT), 0, s>>>(dv, dwr, nr, p, dx, 0);  // Gv = V^H Gamma_R V
     k_eig_gram<<<gg, dim3(kGT, kGT), 0, s>>>(dw, dwl, nl, p, dx, 1);  // X = Gv o (W^H Gamma_L W)
+    if (prof && rc == TRANSEC_OK) cudaEventRecord(ev[1], s);
     // energies per block: as many as 160 KB of shared memory holds for g, up to 8
     const int eb = (int)std::max<long long>(1, std::min<long long>(kEB, (160LL * 1024) / (16LL * p)));
     const size_t smem = (size_t)eb * p * sizeof(double2);
     ck(cudaFuncSetAttribute(k_eig_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (rc == TRANSEC_OK) k_eig_sum<<<(unsigned)((ne + eb - 1) / eb), 256, smem, s>>>(dx, dl, p, de, ne, eb, dt);
+    if (prof && rc == TRANSEC_OK) cudaEventRecord(ev[2], s);
     ctx->launches += 3;
     ck(cudaGetLastError());
     ck(cudaMemcpyAsync(T_out, dt, (size_t)ne * sizeof(double), cudaMemcpyDeviceToHost, s));
     ck(cudaStreamSynchronize(s));
+    if (prof && rc == TRANSEC_OK) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventElapsedTime(&a, ev[0], ev[1]) == cudaSuccess) ctx->eig_gram_ms += a;
+      if (cudaEventElapsedTime(&b, ev[1], ev[2]) == cudaSuccess) ctx->eig_sum_ms += b;
+    }
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
   }
   cudaFree(dv); cudaFree(dw); cudaFree(dx); cudaFree(dl); cudaFree(dwr); cudaFree(dwl); cudaFree(de); cudaFree(dt);
   cudaGetLastError();
   if (prev >= 0) cudaSetDevice(prev);
   return rc;
+}
+
+int transec_eigen_stats(const transec_ctx* ctx, double* gram_ms, double* sum_ms) {
+  if (!ctx) return TRANSEC_EINVAL;
+  if (gram_ms) *gram_ms = ctx->eig_gram_ms;
+  if (sum_ms) *sum_ms = ctx->eig_sum_ms;
+  return TRANSEC_OK;
 }
 
 }  // extern "C"

@@ -120,6 +120,7 @@ struct transec_ctx {
   long long sweep_stencil_launches = 0, sweep_shift_launches = 0;
   long long sweep_fp64_redone = 0;  // double-float results solved again in FP64
   long long sweep_guard_redone = 0;  // sketch results computed again with a larger sketch
+  double eig_gram_ms = 0, eig_sum_ms = 0;  // eigen route (profile): Gram matrices, eigen-sums
   double sweep_stencil_df_ms = 0, sweep_shift_df_ms = 0;  // the double-float runs' kernels
   long long sweep_stencil_df_launches = 0, sweep_shift_df_launches = 0;
 };
