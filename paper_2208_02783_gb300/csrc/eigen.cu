@@ -33,12 +33,14 @@ __device__ inline double2 zcmul(double2 a, double2 b) {  // conj(a) b
 
 constexpr int kGT = 16;  // Gram tile
 
-// out[m][n] (= or *=) sum_i w_i conj(A[i][m]) A[i][n], A row-major [rows][p].
-// grid (ceil(p/16), ceil(p/16)), block 16 x 16
+// out[m][n] (= or *=) sum_i w_i conj(A[i][m]) A[i][n], A row-major [rows][p].  The
+// matrix is Hermitian: only the tiles on and above the diagonal are computed, and each
+// writes its mirror image conj(.) as well.  grid (ceil(p/16), ceil(p/16)), block 16 x 16
 __global__ void __launch_bounds__(kGT * kGT) k_eig_gram(const double2* A, const double* wgt, long long rows, int p,
                                                       double2* out, int multiply) {
   __shared__ double2 sa[kGT][kGT + 1], sb[kGT][kGT + 1];
   const int tx = threadIdx.x, ty = threadIdx.y;
+  if (blockIdx.y > blockIdx.x) return;  // below the diagonal: written by the mirror tile
   const int m0 = blockIdx.y * kGT, n0 = blockIdx.x * kGT;
   double2 acc = make_double2(0.0, 0.0);
   for (long long i0 = 0; i0 < rows; i0 += kGT) {
@@ -58,7 +60,13 @@ __global__ void __launch_bounds__(kGT * kGT) k_eig_gram(const double2* A, const 
     __syncthreads();
   }
   const int m = m0 + ty, n = n0 + tx;
-  if (m < p && n < p) out[(long long)m * p + n] = multiply ? zmul(out[(long long)m * p + n], acc) : acc;
+  if (m < p && n < p) {
+    out[(long long)m * p + n] = multiply ? zmul(out[(long long)m * p + n], acc) : acc;
+    if (blockIdx.y != blockIdx.x) {  // the mirror element of an off-diagonal tile
+      const double2 c = make_double2(acc.x, -acc.y);
+      out[(long long)n * p + m] = multiply ? zmul(out[(long long)n * p + m], c) : c;
+    }
+  }
 }
 
 constexpr int kEB = 8;  // energies per block at most
