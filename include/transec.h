@@ -115,11 +115,12 @@ typedef struct transec_solver_opts {
                          precision = TRANSEC_PREC_DF64, a potential that passes the
                          inversion check of transec_set_potential, nx <= 32 and
                          nx * ny <= 896; other entry points ignore it.  Default 0 */
-  double sketch_guard; /* transec_transmission_sketch with transpose-BiCG runs: a result
-                         whose two independent estimates differ by more,
-                         |T(E, k) - T(E, -k)| > sketch_guard, is computed again with a
-                         sketch of twice the sizes (up to 32 + 64) and a fresh draw, up to
-                         three times; default 1e-7 (a tenth of the 1e-6 bar on T),
+  double sketch_guard; /* transec_transmission_sketch: a result whose sketch may miss more
+                         of T than this (the missed-energy estimate of miss_out), or, with
+                         transpose-BiCG runs, whose two independent estimates differ by
+                         more, |T(E, k) - T(E, -k)| > sketch_guard, is computed again with
+                         a sketch of twice the sizes (up to 32 + 64) and a fresh draw, up
+                         to three times; default 1e-7 (a tenth of the 1e-6 bar on T),
                          negative = never */
 } transec_solver_opts;
 
@@ -435,17 +436,22 @@ int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, in
  * mirrored, so T_minus equals T to rounding and is no independent estimate; EINVAL
  * when opts.psym is set with another precision, a potential that is not
  * inversion-symmetric (relative gap above 1e-12) or a plane too large for one tile.
- * The FP64 re-solve of failed results uses transpose BiCG.  Without opts.psym, results
- * whose T and T_minus differ by more than opts.sketch_guard are computed again with a
- * doubled sketch (the a-posteriori check acting); rank_out then reports the larger
- * sketch's rank and iters_out adds its iterations.  Host arrays.
+ * The FP64 re-solve of failed results uses transpose BiCG.  miss_out (may be NULL) =
+ * 4 ||(1 - P) y||^2 for the last LEFT run's column y = M omega and P the projector on
+ * the span of the other LEFT columns: since E ||(1 - P) M omega||^2 = ||(1 - P) M||_F^2
+ * for unit-modulus omega, it estimates the part of T = 4 ||M||_F^2 outside the span of
+ * s_left - 1 random directions (the larger of the two signs of k).  Results with
+ * miss_out above opts.sketch_guard, or (without opts.psym) with T and T_minus apart by
+ * more, are computed again with a doubled sketch (the a-posteriori checks acting);
+ * rank_out, miss_out then report the larger sketch and iters_out adds its
+ * iterations.  Host arrays.
  * Errors: EINVAL, ESTATE, ENOMEM, ECUDA, ETIMEOUT; per-result ENOCONV / EBREAKDOWN with
  * T = NaN.
  */
 int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies, int nrep,
                                 const int* ik, int s_left, int s_right, unsigned long long seed,
                                 double* T_out, double* T_minus_out, int* rank_out, int* status_out,
-                                int* iters_out);
+                                int* iters_out, double* miss_out);
 
 /*
  * The paper's eigen route, its per-energy stage (Sec. II.A, Eqs.

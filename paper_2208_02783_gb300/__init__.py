@@ -139,8 +139,8 @@ class Transec:
     def transmission_sketch(self, energies, ik, s_left=16, s_right=32, seed=0):
         """Full-trace T(E, k) and T(E, -k) for the k indices ``ik`` over a window of
         energies from the two-sided sketch: arrays of shape (len(ik), len(energies))."""
-        T, tm, rk, st, it = transec_transmission_sketch(self.ctx, energies, ik, s_left, s_right, seed)
-        return {"T": T, "T_minus": tm, "rank": rk, "status": st, "iters": it}
+        T, tm, rk, st, it, ms = transec_transmission_sketch(self.ctx, energies, ik, s_left, s_right, seed)
+        return {"T": T, "T_minus": tm, "rank": rk, "status": st, "iters": it, "miss": ms}
 
     def sweep_stats(self) -> dict:
         return transec_sweep_stats(self.ctx)

@@ -101,7 +101,7 @@ _SIGS = {
     "transec_shifted_column": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_longlong, _P, _P, _P, _P]),
     "transec_shifted_columns": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, _P, _P, _P, _P, _P]),
     "transec_transmission_sketch": (C.c_int, [_P, C.c_int, _P, C.c_int, _P, C.c_int, C.c_int, C.c_ulonglong,
-                                              _P, _P, _P, _P, _P]),
+                                              _P, _P, _P, _P, _P, _P]),
     "transec_sweep_stats": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                       C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                       C.POINTER(C.c_longlong), C.POINTER(C.c_double), C.POINTER(C.c_longlong),
@@ -568,7 +568,7 @@ def transec_shifted_columns(ctx, energies, ik, cols):
 
 def transec_transmission_sketch(ctx, energies, ik, s_left=16, s_right=32, seed=0):
     """Full-trace T(E, k) and T(E, -k) by the two-sided sketch; returns
-    (T, T_minus, rank, status, iters) host arrays of shape (len(ik), ne)."""
+    (T, T_minus, rank, status, iters, miss) host arrays of shape (len(ik), ne)."""
     e = np.ascontiguousarray(energies, np.float64)
     k = np.ascontiguousarray(ik, np.int32)
     ne, nr = e.size, k.size
@@ -577,11 +577,12 @@ def transec_transmission_sketch(ctx, energies, ik, s_left=16, s_right=32, seed=0
     rk = np.zeros((nr, ne), np.int32)
     so = np.zeros((nr, ne), np.int32)
     it = np.zeros((nr, ne), np.int32)
+    ms = np.zeros((nr, ne))
     vp = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
     st = load().transec_transmission_sketch(ctx, ne, vp(e), nr, vp(k), int(s_left), int(s_right), int(seed),
-                                            vp(T), vp(Tm), vp(rk), vp(so), vp(it))
+                                            vp(T), vp(Tm), vp(rk), vp(so), vp(it), vp(ms))
     _check(ctx, st, "transec_transmission_sketch", allow=(ENOCONV, EBREAKDOWN))
-    return T, Tm, rk, so, it
+    return T, Tm, rk, so, it, ms
 
 
 def transec_sweep_stats(ctx) -> dict:

@@ -654,6 +654,9 @@ struct GnArgs {
   int* rank;               // [rep][ne][2]
   int* status;             // [rep][ne][2]
   double drop;             // relative norm below which a column of Y adds no direction
+  double* miss;            // [rep][ne][2] 4 ||(1 - P) y_last||^2: the energy of M outside the span
+                           // of the first s_left - 1 columns of Y (an estimate of what the
+                           // sketch misses of T; E ||(1 - P) M omega||^2 = ||(1 - P) M||_F^2)
   int psym;                // P-symmetric runs: the +k rows of W belong to P_k psi
   int nx, ny;
   const Slot* slots;
@@ -688,6 +691,7 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
   __shared__ double s_nrm0;
   __shared__ double2 s_v[kGnMaxR];
   __shared__ int s_cols[kGnMaxL];
+  __shared__ double s_miss;
   const int s = blockIdx.x, rep = blockIdx.y, sign = blockIdx.z;
   const int hY = sign, hW = 1 - sign;  // +k: primal of LEFT, shadow of RIGHT; -k: swapped
   const int sl = a.sl, sr = a.sr;
@@ -707,6 +711,7 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
   if (s_status != kOK) {
     if (threadIdx.x == 0) {
       a.T[o_out] = __longlong_as_double(0x7ff8000000000000LL);
+      a.miss[o_out] = __longlong_as_double(0x7ff8000000000000LL);
       a.rank[o_out] = 0;
       a.status[o_out] = s_status;
     }
@@ -775,6 +780,7 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
     gn_block_sum<1>(v, s_red, red);
     const double nrm = sqrt(s_red[0]);
     const int keep = nrm > a.drop * s_nrm0 && nrm > 0.0;
+    if (c == sl - 1 && threadIdx.x == 0) s_miss = 4.0 * nrm * nrm;
     if (keep) {
       const double inv = 1.0 / nrm;
       for (long long u = threadIdx.x; u < nR; u += blockDim.x) y[u] = make_double2(inv * y[u].x, inv * y[u].y);
@@ -938,6 +944,7 @@ __global__ void __launch_bounds__(256) k_ms_gn(const GnArgs a) {
       }
     }
     a.T[o_out] = bad ? __longlong_as_double(0x7ff8000000000000LL) : 4.0 * tr;
+    a.miss[o_out] = s_miss;
     a.rank[o_out] = r;
     a.status[o_out] = bad ? kEBREAKDOWN : kOK;
   }
@@ -1395,7 +1402,7 @@ namespace {
 
 // Results of one multi-shift call, row-major [item or k group][energy].
 struct SweepOut {
-  std::vector<double> t, tm;
+  std::vector<double> t, tm, miss;
   std::vector<int> it, st, rank;
 };
 
@@ -1485,10 +1492,11 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
   if (rc != TRANSEC_OK) return rc;
   SweepBufs& B = *ctx->sweep;
   int *d_rs = nullptr, *d_rank = nullptr, *d_st = nullptr;
-  double* d_T = nullptr;
+  double *d_T = nullptr, *d_miss = nullptr;
   const size_t nout = (size_t)nrep * ne * 2;
   cudaError_t e = cudaMalloc(&d_rs, run_slot.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&d_T, nout * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_miss, nout * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&d_rank, nout * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&d_st, nout * sizeof(int));
   if (e == cudaSuccess)
@@ -1521,7 +1529,7 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
     ga.np = B.no; ga.no = B.no; ga.nxy = ctx->g.nxy; ga.ne = ne; ga.sl = s_left; ga.sr = s_right;
     ga.lplanes = ctx->d_lplanes; ga.rplanes = ctx->d_rplanes; ga.nlp = (int)ctx->lplanes.size();
     ga.nrp = (int)ctx->rplanes.size(); ga.gl = ctx->d_gl; ga.gr = ctx->d_gr; ga.T = d_T; ga.rank = d_rank;
-    ga.status = d_st; ga.drop = 1e-13;
+    ga.status = d_st; ga.drop = 1e-13; ga.miss = d_miss;
     ga.psym = psym ? 1 : 0; ga.nx = ctx->g.nx; ga.ny = ctx->g.ny; ga.slots = B.slots; ga.phase = ctx->d_phase;
     if (dfm) k_ms_gn<float4><<<dim3((unsigned)ne, (unsigned)nrep, 2), 256, smem, ctx->s>>>(ga);
     else k_ms_gn<double2><<<dim3((unsigned)ne, (unsigned)nrep, 2), 256, smem, ctx->s>>>(ga);
@@ -1529,9 +1537,10 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && prof) cudaEventRecord(g1, ctx->s);
-  std::vector<double> T(nout);
+  std::vector<double> T(nout), miss(nout);
   std::vector<int> rk(nout), stt(nout);
   if (e == cudaSuccess) e = cudaMemcpyAsync(T.data(), d_T, nout * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(miss.data(), d_miss, nout * sizeof(double), cudaMemcpyDeviceToHost, ctx->s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(rk.data(), d_rank, nout * sizeof(int), cudaMemcpyDeviceToHost, ctx->s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(stt.data(), d_st, nout * sizeof(int), cudaMemcpyDeviceToHost, ctx->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->s);
@@ -1546,6 +1555,7 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
   if (e == cudaSuccess) e = cudaMemcpy(hsh.data(), B.sh, hsh.size() * sizeof(MsShift), cudaMemcpyDeviceToHost);
   cudaFree(d_rs);
   cudaFree(d_T);
+  cudaFree(d_miss);
   cudaFree(d_rank);
   cudaFree(d_st);
   if (e != cudaSuccess) {
@@ -1555,6 +1565,7 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
   const size_t m = (size_t)nrep * ne;
   out.t.resize(m);
   out.tm.resize(m);
+  out.miss.resize(m);
   out.rank.resize(m);
   out.st.resize(m);
   out.it.resize(m);
@@ -1564,6 +1575,7 @@ int sketch_solve(transec_ctx* ctx, const std::vector<double>& es, const std::vec
       const size_t u = (size_t)r * ne + s;
       out.t[u] = T[o];
       out.tm[u] = T[o + 1];
+      out.miss[u] = std::max(miss[o], miss[o + 1]);
       out.rank[u] = std::min(rk[o], rk[o + 1]);
       out.st[u] = ms_severity(stt[o]) >= ms_severity(stt[o + 1]) ? stt[o] : stt[o + 1];
       int mx = 0;
@@ -1674,7 +1686,8 @@ int transec_shifted_columns(transec_ctx* ctx, int ne, const double* energies, in
 
 int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies, int nrep, const int* ik,
                                 int s_left, int s_right, unsigned long long seed, double* T_out,
-                                double* T_minus_out, int* rank_out, int* status_out, int* iters_out) {
+                                double* T_minus_out, int* rank_out, int* status_out, int* iters_out,
+                                double* miss_out) {
   if (!ctx) return TRANSEC_EINVAL;
   if (!ctx->have_v || !ctx->have_abc || !ctx->have_k)
     return ms_fail(ctx, TRANSEC_ESTATE, "potential, absorbing boundary and k-mesh must be set");
@@ -1721,19 +1734,24 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
         if (!redo_status(out.st[u])) continue;
         out.t[u] = o2.t[v];
         out.tm[u] = o2.tm[v];
+        out.miss[u] = o2.miss[v];
         out.rank[u] = o2.rank[v];
         out.st[u] = o2.st[v];
         out.it[u] += o2.it[v];
         ctx->sweep_fp64_redone += 1;
       }
   }
-  // the a-posteriori check acting: results whose independent +-k estimates disagree by
-  // more than the guard are computed again with a sketch of twice the sizes
-  for (int round = 0; !psym && ctx->opts.sketch_guard > 0 && round < 3; ++round) {
+  // the a-posteriori checks acting: results whose independent +-k estimates disagree by
+  // more than the guard, or whose sketch may miss more than the guard of T (the energy
+  // of M outside the span of all but the last LEFT column), are computed again with a
+  // sketch of twice the sizes (for P-symmetric runs only the second check applies)
+  const double guard = ctx->opts.sketch_guard;
+  for (int round = 0; guard > 0 && round < 3; ++round) {
     std::vector<int> st2((size_t)nrep * ne, TRANSEC_OK);
     bool any = false;
     for (size_t u = 0; u < st2.size(); ++u)
-      if (out.st[u] == TRANSEC_OK && !(std::fabs(out.t[u] - out.tm[u]) <= ctx->opts.sketch_guard)) {
+      if (out.st[u] == TRANSEC_OK &&
+          (!(out.miss[u] <= guard) || (!psym && !(std::fabs(out.t[u] - out.tm[u]) <= guard)))) {
         st2[u] = TRANSEC_ENOCONV;  // marks the result for failed_parts
         any = true;
       }
@@ -1746,7 +1764,7 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
     for (int s : ecols) e3.push_back(es[s]);
     for (int r : rows) k3.push_back(hik[r]);
     SweepOut o3;
-    rc = sketch_solve(ctx, e3, k3, s_left, s_right, splitmix64(seed + 0x9E37ULL * (round + 1)), o3);
+    rc = sketch_solve(ctx, e3, k3, s_left, s_right, splitmix64(seed + 0x9E37ULL * (round + 1)), o3, psym);
     if (rc != TRANSEC_OK) return rc;
     for (size_t a = 0; a < rows.size(); ++a)
       for (size_t b = 0; b < ecols.size(); ++b) {
@@ -1756,6 +1774,7 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
         if (o3.st[v] != TRANSEC_OK) continue;  // keep the smaller sketch's estimate
         out.t[u] = o3.t[v];
         out.tm[u] = o3.tm[v];
+        out.miss[u] = o3.miss[v];
         out.rank[u] = o3.rank[v];
         ctx->sweep_guard_redone += 1;
       }
@@ -1767,6 +1786,7 @@ int transec_transmission_sketch(transec_ctx* ctx, int ne, const double* energies
     if (rank_out) rank_out[u] = out.rank[u];
     if (status_out) status_out[u] = out.st[u];
     if (iters_out) iters_out[u] = out.it[u];
+    if (miss_out) miss_out[u] = out.miss[u];
     if (ms_severity(out.st[u]) > ms_severity(worst)) worst = out.st[u];
   }
   if (worst != TRANSEC_OK) ctx->err = std::string("some (E, k) failed: ") + transec_status_string(worst);
