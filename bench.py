@@ -60,9 +60,9 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.070e9 * 2 / 1e12
 # FMA, one each): 128 FP32 lanes per SM x 152 SMs x 2070 MHz
 FP32_OPS_PEAK_T = 128 * 152 * 2.070e9 / 1e12
 # DRAM bytes per point-half of one double-float stencil launch, from the ncu capture in
-# profiles/k_stencil_df_cu_bulk.md (583.9 MB for 9.216 M point-halves, 8 + 16 runs, slabs
-# of 120 planes); reset to None whenever the kernel changes
-DF_STENCIL_DRAM_PER_POINT_HALF = 583.9e6 / 9.216e6
+# profiles/k_stencil_df_cu_bulk.md (294.4 MB for 4.608 M point-halves, 4 + 8 runs, slabs
+# of 40 planes); reset to None whenever the kernel changes
+DF_STENCIL_DRAM_PER_POINT_HALF = 294.4e6 / 4.608e6
 
 
 def stencil_flops_per_point(order: int) -> int:
