@@ -305,6 +305,11 @@ int transec_unet_create(transec_unet** out, int device, int nx, int ny, int nz,
  * (cout).  set_params(NULL) only resets the optimiser state. */
 int transec_unet_n_params(const transec_unet* u, long long* n);
 int transec_unet_set_params(transec_unet* u, const float* params);
+/* Zero the output layer's weights (its bias is kept) and reset the optimiser state: the
+ * learned preconditioner's starting point (the first Adam steps then learn a
+ * correlation with the target instead of shrinking a random output of the wrong
+ * scale).  Errors: EINVAL, ECUDA. */
+int transec_unet_zero_output(transec_unet* u);
 int transec_unet_get_params(transec_unet* u, float* params);
 /* out[v][0..1] = network(in[v][0..3]) for every voxel v = x + nx(y + ny z); FP32, device
  * (on_device != 0) or host memory. */

@@ -21,7 +21,7 @@ from .binding import (  # noqa: F401
     transec_sweep_stats, transec_transmission_sketch, transec_unet_create, transec_unet_destroy,
     transec_unet_dims, transec_unet_forward, transec_unet_get_params, transec_unet_n_params,
     transec_unet_set_params, transec_unet_set_path, transec_unet_train_operator, transec_unet_train_step,
-    transec_eigen_transmission,
+    transec_eigen_transmission, transec_unet_zero_output,
 )
 
 
@@ -190,12 +190,7 @@ class LearnedPreconditioner:
         nz, ny, nx = transec.shape
         self.transec = transec
         self.net = transec_unet_create(device, nx, ny, nz, seed)
-        # the output layer starts at zero weights: the first steps then learn a correlation
-        # with the target instead of shrinking a random output of the wrong scale
-        p = transec_unet_get_params(self.net)
-        w_out = 27 * 2 * 16
-        p[-(w_out + 2):-2] = 0.0
-        transec_unet_set_params(self.net, p)
+        transec_unet_zero_output(self.net)
 
     def train(self, steps, e_lo, e_hi, lr=1e-3, seed=0, source="krylov"):
         """Adam steps on pairs (r = A e, e) from Krylov iterates ("krylov") or random

@@ -109,6 +109,7 @@ _SIGS = {
                                       C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]),
     "transec_unet_destroy": (None, [_P]),
     "transec_unet_set_path": (C.c_int, [_P, C.c_int]),
+    "transec_unet_zero_output": (C.c_int, [_P]),
     "transec_eigen_transmission": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int, _P, _P]),
     "transec_eigen_stats": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "transec_unet_conv3d": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P,
@@ -448,6 +449,10 @@ def transec_eigen_stats(ctx) -> dict:
     a, b = C.c_double(), C.c_double()
     _check(ctx, load().transec_eigen_stats(ctx, C.byref(a), C.byref(b)), "transec_eigen_stats")
     return {"gram_ms": a.value, "sum_ms": b.value}
+
+
+def transec_unet_zero_output(u):
+    _ucheck(u, load().transec_unet_zero_output(u), "transec_unet_zero_output")
 
 
 def transec_unet_set_path(u, path):

@@ -361,6 +361,21 @@ int transec_unet_set_params(transec_unet* u, const float* params) {
   return TRANSEC_OK;
 }
 
+int transec_unet_zero_output(transec_unet* u) {
+  if (!u) return TRANSEC_EINVAL;
+  Dev dg(u->device);
+  const Layer& L = u->L[OUT];
+  UCK(cudaMemsetAsync(u->p + L.w_off, 0, 27LL * L.cout_p * L.cin_p * sizeof(float), u->s));
+  UCK(cudaMemsetAsync(u->m, 0, u->np_pad * sizeof(float), u->s));
+  UCK(cudaMemsetAsync(u->v, 0, u->np_pad * sizeof(float), u->s));
+  u->step = 0;
+  k_to_bf16<<<grid_for(u->nw_pad), 256, 0, u->s>>>(u->p, u->wbf, u->nw_pad);
+  flip_all(u);
+  UCK(cudaGetLastError());
+  UCK(cudaStreamSynchronize(u->s));
+  return TRANSEC_OK;
+}
+
 static int get_flat(transec_unet* u, const float* src, float* params) {
   std::vector<float> hp(u->np_pad);
   UCK(cudaMemcpyAsync(hp.data(), src, u->np_pad * sizeof(float), cudaMemcpyDeviceToHost, u->s));

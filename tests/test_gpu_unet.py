@@ -207,3 +207,22 @@ def test_training_reduces_loss():
         assert losses[-1] < 0.5 * losses[0], losses[::10]
     finally:
         pkg.binding.transec_unet_destroy(u)
+
+
+def test_zero_output_layer():
+    """transec_unet_zero_output zeroes the output layer's weights (the learned
+    preconditioner's start) and leaves every other parameter as it was."""
+    need_gpu()
+    pkg = library()
+    u, x, t, params = _setup(pkg, SHAPES[0], seed=9)
+    try:
+        pkg.binding.transec_unet_zero_output(u)
+        after = _unflatten(pkg.binding.transec_unet_get_params(u))
+        for name, *_ in ref.LAYERS:
+            if name == "out":
+                assert np.all(after["out.w"] == 0) and np.array_equal(after["out.b"], params["out.b"])
+            else:
+                assert np.array_equal(after[name + ".w"], params[name + ".w"])
+                assert np.array_equal(after[name + ".b"], params[name + ".b"])
+    finally:
+        pkg.binding.transec_unet_destroy(u)
