@@ -761,9 +761,9 @@ def run_eigen_stage(args):
                    "kernel_ms": es},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
-                     # DRAM bytes of one Gram launch at 1 024 eigenpairs, from the ncu capture in
-                     # profiles/k_eig_gram_cu_bulk.md (4.80 GB read + 20.7 MB written)
-                     "traffic": 4.817e9 if p == 1024 else None,
+                     # the capture in profiles/k_eig_gram_cu_bulk.md predates the kernel's fused
+                     # inner loop: no traffic figure for the current kernel
+                     "traffic": None,
                      "kernel": "k_eig_gram (complex FP64 Hermitian Gram matrices, one triangle of 16 x 16 "
                                "shared-memory tiles)",
                      "flops": {"gram": gram_flops, "sum": sum_flops},

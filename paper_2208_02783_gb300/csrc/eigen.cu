@@ -52,10 +52,12 @@ __global__ void __launch_bounds__(kGT * kGT) k_eig_gram(const double2* A, const 
     sb[ty][tx] = make_double2(w * bv.x, w * bv.y);
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kGT; ++k) {
-      const double2 c = zcmul(sa[k][ty], sb[k][tx]);
-      acc.x += c.x;
-      acc.y += c.y;
+    for (int k = 0; k < kGT; ++k) {  // acc += conj(a) b as four fused multiply-adds
+      const double2 a = sa[k][ty], b = sb[k][tx];
+      acc.x = fma(a.x, b.x, acc.x);
+      acc.x = fma(a.y, b.y, acc.x);
+      acc.y = fma(a.x, b.y, acc.y);
+      acc.y = fma(-a.y, b.x, acc.y);
     }
     __syncthreads();
   }
@@ -99,10 +101,12 @@ __global__ void __launch_bounds__(256) k_eig_sum(const double2* X, const double2
       const double2 x = X[(long long)m * p + n];
 #pragma unroll
       for (int j = 0; j < kEB; ++j)
-        if (j < nb) {
-          const double2 c = zmul(x, gsh[j * p + n]);
-          y[j].x += c.x;
-          y[j].y += c.y;
+        if (j < nb) {  // y += x g as four fused multiply-adds
+          const double2 g = gsh[j * p + n];
+          y[j].x = fma(x.x, g.x, y[j].x);
+          y[j].x = fma(-x.y, g.y, y[j].x);
+          y[j].y = fma(x.x, g.y, y[j].y);
+          y[j].y = fma(x.y, g.x, y[j].y);
         }
     }
 #pragma unroll
