@@ -50,7 +50,7 @@ WORKLOAD_RH = ("Rh periodic point contact [001] a=7.18, 3x3 cells, 60x60x512 h=0
                "4x4 MP k-mesh, 512 energies in E_F+-0.3 Ha, tol 1e-10")
 HBM_FALLBACK_GBS = 6800.0
 # DRAM bytes per point-half of one FP64 stencil launch, from the ncu capture in
-# profiles/k_stencil_fp64_cu_bulk.md (900.5 MB for 12.29 M point-halves); scaled by the
+# ncu capture of the FP64 stencil on the bulk Cu workload (900.5 MB for 12.29 M point-halves); scaled by the
 # point-halves of each launch for the roofline's traffic.  Reset to None whenever the
 # kernel changes.
 FP64_STENCIL_DRAM_PER_POINT_HALF = 900.5e6 / 12.288e6
@@ -60,7 +60,7 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.070e9 * 2 / 1e12
 # FMA, one each): 128 FP32 lanes per SM x 152 SMs x 2070 MHz
 FP32_OPS_PEAK_T = 128 * 152 * 2.070e9 / 1e12
 # DRAM bytes per point-half of one double-float stencil launch, from the ncu capture in
-# profiles/k_stencil_df_cu_bulk.md (294.4 MB for 4.608 M point-halves, 4 + 8 runs, slabs
+# ncu capture of the double-float stencil on the bulk Cu workload (294.4 MB for 4.608 M point-halves, 4 + 8 runs, slabs
 # of 40 planes); reset to None whenever the kernel changes
 DF_STENCIL_DRAM_PER_POINT_HALF = 294.4e6 / 4.608e6
 
@@ -761,7 +761,7 @@ def run_eigen_stage(args):
                    "kernel_ms": es},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved / FP64_PEAK_TFLOPS,
-                     # the capture in profiles/k_eig_gram_cu_bulk.md predates the kernel's fused
+                     # the ncu capture of the Gram kernel predates the kernel's fused
                      # inner loop: no traffic figure for the current kernel
                      "traffic": None,
                      "kernel": "k_eig_gram (complex FP64 Hermitian Gram matrices, one triangle of 16 x 16 "
