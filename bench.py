@@ -49,8 +49,8 @@ WORKLOAD_RH = ("Rh periodic point contact [001] a=7.18, 3x3 cells, 60x60x512 h=0
                "V0=1.4 sigma=0.95, hyperboloid neck r0=4, 1% vacancies, 64-plane CAPs 0.3 Ha, "
                "4x4 MP k-mesh, 512 energies in E_F+-0.3 Ha, tol 1e-10")
 HBM_FALLBACK_GBS = 6800.0
-# DRAM bytes per point-half of one FP64 stencil launch, from the ncu capture in
-# ncu capture of the FP64 stencil on the bulk Cu workload (900.5 MB for 12.29 M point-halves); scaled by the
+# DRAM bytes per point-half of one FP64 stencil launch, from the ncu capture of that
+# kernel on the bulk Cu workload (900.5 MB for 12.29 M point-halves); scaled by the
 # point-halves of each launch for the roofline's traffic.  Reset to None whenever the
 # kernel changes.
 FP64_STENCIL_DRAM_PER_POINT_HALF = 900.5e6 / 12.288e6
@@ -59,9 +59,9 @@ FP64_PEAK_TFLOPS = 2 * 152 * 2.070e9 * 2 / 1e12
 # FP32 pipe roofline of the double-float stencil, in FP32 operations (add, multiply or
 # FMA, one each): 128 FP32 lanes per SM x 152 SMs x 2070 MHz
 FP32_OPS_PEAK_T = 128 * 152 * 2.070e9 / 1e12
-# DRAM bytes per point-half of one double-float stencil launch, from the ncu capture in
-# ncu capture of the double-float stencil on the bulk Cu workload (294.4 MB for 4.608 M point-halves, 4 + 8 runs, slabs
-# of 40 planes); reset to None whenever the kernel changes
+# DRAM bytes per point-half of one double-float stencil launch, from the ncu capture of
+# that kernel on the bulk Cu workload (294.4 MB for 4.608 M point-halves, 4 + 8 runs,
+# slabs of 40 planes); reset to None whenever the kernel changes
 DF_STENCIL_DRAM_PER_POINT_HALF = 294.4e6 / 4.608e6
 
 
