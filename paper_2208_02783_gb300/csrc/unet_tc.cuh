@@ -169,24 +169,35 @@ __global__ void __launch_bounds__(128) k_conv_tc(const ConvTcArgs a) {
     }
     if (!__syncthreads_and(ok)) break;
     // input box, zero outside the volume and past the box; asynchronous 16-byte copies,
-    // all of a thread's copies in flight at once
+    // all of a thread's copies in flight at once.  A thread walks the positions t, t + S,
+    // ... (S threads) with its box coordinates advanced incrementally (no division per
+    // copy) and copies every channel group of a position.
     const uint32_t box_s = tc_smem_u32(box), w_s = tc_smem_u32(wsm);
-    for (int idx = t; idx < npos * nch; idx += blockDim.x) {
-      const int pos = idx / nch, ch = idx - pos * nch;
-      const int zb = pos / P, rem = pos - zb * P;
-      const int yb = rem / XH, xb = rem - yb * XH;
-      const int gx = xb - 1, gy = yb - 1, gz = z0 - 1 + zb;
-      const bool in = zb < a.bz + 2 && gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
-      const bf16* src =
-          in ? a.x + ((long long)gx + (long long)nx * (gy + (long long)ny * gz)) * a.cin + c0 + ch * 8 : a.x;
-      tc_copy16(box_s + (uint32_t)(((size_t)ch * npos + pos) * 16), src, in ? 16u : 0u);
+    {
+      const int S = blockDim.x;
+      const int DX = S % XH, DY = (S / XH) % YH, DZ = S / P;
+      int zb = t / P, yb = (t - zb * P) / XH, xb = t - zb * P - yb * XH;
+      for (int pos = t; pos < npos; pos += S) {
+        const int gx = xb - 1, gy = yb - 1, gz = z0 - 1 + zb;
+        const bool in = zb < a.bz + 2 && gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+        const bf16* src =
+            in ? a.x + ((long long)gx + (long long)nx * (gy + (long long)ny * gz)) * a.cin + c0 : a.x;
+        const uint32_t dst = box_s + (uint32_t)pos * 16u;
+        for (int ch = 0; ch < nch; ++ch)
+          tc_copy16(dst + (uint32_t)ch * (uint32_t)npos * 16u, in ? src + ch * 8 : a.x, in ? 16u : 0u);
+        xb += DX;
+        if (xb >= XH) { xb -= XH; ++yb; }
+        yb += DY;
+        if (yb >= YH) { yb -= YH; ++zb; }
+        zb += DZ;
+      }
     }
-    // the pass's weights of every tap
-    for (int idx = t; idx < 27 * cout * nch; idx += blockDim.x) {
-      const int ch = idx % nch, rest = idx / nch;
-      const int o = rest % cout, tap = rest / cout;
-      tc_copy16(w_s + (uint32_t)((((size_t)tap * nch + ch) * cout + o) * 16),
-                a.w + ((long long)tap * cout + o) * a.cin + c0 + ch * 8, 16u);
+    // the pass's weights of every tap: one row (tap, output channel) per thread step
+    for (int row = t; row < 27 * cout; row += blockDim.x) {
+      const int tap = row / cout, o = row - tap * cout;
+      const bf16* src = a.w + (long long)row * a.cin + c0;
+      const uint32_t dst = w_s + (uint32_t)((tap * nch * cout + o) * 16);
+      for (int ch = 0; ch < nch; ++ch) tc_copy16(dst + (uint32_t)(ch * cout * 16), src + ch * 8, 16u);
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
