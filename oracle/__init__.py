@@ -16,6 +16,7 @@ transmission T(E, k) by dense LU, sparse LU or plain COCG / transpose BiCG; k-av
 closed_form  separable V = 0 transmission and open-channel (mode) counting
 unet         NumPy forward/backward of the learned preconditioner's network
 eigen        the paper's eigen route: eigenpairs of H_k - i Gamma, transformed CAPs, eigen-sum
+sketch       the two-sided randomized sketch of T with the library's splitmix64 draws
 
 Every function is pinned by tests/test_oracle_*.py against facts fixed by the paper
 or by mathematics (polynomial exactness, Hermiticity, separable closed form, the

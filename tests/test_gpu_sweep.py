@@ -266,3 +266,25 @@ def test_sketch_guard_redoes_disagreeing_results():
         for s, e in enumerate(energies):
             tp, _ = transmission_dense(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf)
             assert abs(r["T"][0, s] - tp) <= TOL_T
+
+
+def test_sketch_matches_oracle_sketch_with_the_same_draws():
+    """The sketch's arithmetic, not only its limit: with fewer left vectors than the rank
+    of M (a truncated sketch, off the exact T by up to 0.6 here), the GPU's T(E, k),
+    T(E, -k) and missed-energy estimate equal the oracle's two-sided sketch computed
+    with the same splitmix64 draws (FP64 runs, guard off)."""
+    need_gpu()
+    from oracle.sketch import sketch_transmission
+
+    kf = (0.23, -0.37)
+    inst = small_instance(8, 8, 36, 0.4, 4, 8, v_amp=0.2, kfrac=(kf, (-kf[0], -kf[1])), energies=(0.3,), seed=13)
+    g = inst.grid
+    energies = np.array([1.2, 2.0, 3.0])
+    with context(inst, precision=0, sketch_guard=-1.0) as tr:
+        r = tr.transmission_sketch(energies, [0], s_left=3, s_right=6, seed=5)
+    assert np.all(r["status"] == 0), r["status"]
+    for s, e in enumerate(energies):
+        tp, tm, miss = sketch_transmission(g, inst.v, inst.gamma_l, inst.gamma_r, e, kf, 3, 6, 5)
+        assert abs(r["T"][0, s] - tp) <= 1e-6 * max(1.0, tp), (e, r["T"][0, s], tp)
+        assert abs(r["T_minus"][0, s] - tm) <= 1e-6 * max(1.0, tm), (e, r["T_minus"][0, s], tm)
+        assert abs(r["miss"][0, s] - miss) <= 1e-6 * max(1.0, miss), (e, r["miss"][0, s], miss)
